@@ -1,0 +1,186 @@
+"""Complex128 CPU oracle for butterfly tensor completion (arXiv 2510.17734).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The oracle shares no
+code with the CUDA library; both only see the same seeded inputs from
+``synth``.  The arithmetic lives in ``bfc_oracle.c`` (plain serial C99
+``double complex``); this module compiles it with gcc and marshals numpy
+arrays through ctypes.
+
+Functions and the passage each follows:
+  tree_bits, slice_id      Eq. (indices), Sec. 3.1; psi^{-1} and Eq.
+                           (reshaped_tensors), App. A.2
+  num_params               Sec. 2.2 memory count with the App. A.2 reshape
+  eval_entries             Eq. (BF_tensor_rep)
+  rel_err                  Eq. (BF_convergence)
+  objective                Eq. (BF_objective) + lambda/2 ||S||^2 (Sec. 4.1.1)
+  als_sweep                Alg. 1 (complex normal equations)
+  grad                     Eqs. (grad_butterfly_1/_l/_last)
+  embed_lowrank            identity embedding of A B^T (stand-in for Alg. 2)
+  lr_complete              Alg. 1 with L = 0 (low-rank matrix completion,
+                           Sec. 4.2)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bfc_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libbfc_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/libbfc_oracle.so (portable flags,
+    no FMA contraction, so x86 and Arm hosts give identical results)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("train_rel_err", ctypes.c_double),
+                ("objective", ctypes.c_double),
+                ("singular", ctypes.c_int64)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+        lib.bfo_tree_bits.argtypes = [i64, i32, i32, vp]
+        lib.bfo_tree_bits.restype = None
+        lib.bfo_psi_inv.argtypes = [vp, i32]
+        lib.bfo_psi_inv.restype = i64
+        lib.bfo_slice_id.argtypes = [i64, i64, i32, i32, i32]
+        lib.bfo_slice_id.restype = i64
+        lib.bfo_num_params.argtypes = [i64, i32, i32, i32]
+        lib.bfo_num_params.restype = i64
+        lib.bfo_eval.argtypes = [i64, i32, i32, i32, vp, i64, vp, vp, vp]
+        lib.bfo_eval.restype = None
+        lib.bfo_rel_err.argtypes = [i64, i32, i32, i32, vp, i64, vp, vp, vp]
+        lib.bfo_rel_err.restype = dbl
+        lib.bfo_objective.argtypes = [i64, i32, i32, i32, dbl, vp, i64, vp, vp, vp]
+        lib.bfo_objective.restype = dbl
+        lib.bfo_als_sweep.argtypes = [i64, i32, i32, i32, dbl, vp, i64, vp, vp, vp,
+                                      ctypes.POINTER(_Stats)]
+        lib.bfo_als_sweep.restype = i64
+        lib.bfo_grad.argtypes = [i64, i32, i32, i32, dbl, i32, vp, i64, vp, vp, vp, vp, vp]
+        lib.bfo_grad.restype = None
+        lib.bfo_embed_lowrank.argtypes = [i64, i32, i32, i32, i32, vp, vp, vp, vp]
+        lib.bfo_embed_lowrank.restype = None
+        _lib = lib
+        return lib
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_params(n: int, L: int, b: int, r: int) -> int:
+    return int(_load().bfo_num_params(n, L, b, r))
+
+
+def tree_bits(i: int, L: int, b: int) -> list[int]:
+    out = np.zeros(L + 1, dtype=np.int32)
+    _load().bfo_tree_bits(int(i), L, b, _ptr(out))
+    return [int(v) for v in out]
+
+
+def psi_inv(bits) -> int:
+    arr = _i32(bits)
+    return int(_load().bfo_psi_inv(_ptr(arr), len(arr)))
+
+
+def slice_id(i: int, j: int, m: int, L: int, b: int) -> int:
+    return int(_load().bfo_slice_id(int(i), int(j), m, L, b))
+
+
+def eval_entries(n, L, b, r, packed, i, j) -> np.ndarray:
+    packed = _c128(packed)
+    i, j = _i32(i), _i32(j)
+    out = np.zeros(len(i), dtype=np.complex128)
+    _load().bfo_eval(n, L, b, r, _ptr(packed), len(i), _ptr(i), _ptr(j), _ptr(out))
+    return out
+
+
+def rel_err(n, L, b, r, packed, i, j, t) -> float:
+    packed, t = _c128(packed), _c128(t)
+    i, j = _i32(i), _i32(j)
+    return float(_load().bfo_rel_err(n, L, b, r, _ptr(packed), len(i), _ptr(i), _ptr(j), _ptr(t)))
+
+
+def objective(n, L, b, r, lam, packed, i, j, t) -> float:
+    packed, t = _c128(packed), _c128(t)
+    i, j = _i32(i), _i32(j)
+    return float(_load().bfo_objective(n, L, b, r, lam, _ptr(packed), len(i), _ptr(i),
+                                       _ptr(j), _ptr(t)))
+
+
+def als_sweep(n, L, b, r, lam, packed, i, j, t):
+    """One ALS sweep (Alg. 1).  Returns (new_packed, stats dict)."""
+    out = _c128(packed).copy()
+    t = _c128(t)
+    i, j = _i32(i), _i32(j)
+    st = _Stats()
+    _load().bfo_als_sweep(n, L, b, r, lam, _ptr(out), len(i), _ptr(i), _ptr(j), _ptr(t),
+                          ctypes.byref(st))
+    return out, {"train_rel_err": st.train_rel_err, "objective": st.objective,
+                 "singular": int(st.singular)}
+
+
+def grad(n, L, b, r, lam, packed, i, j, t, include_reg=True):
+    """Gradient (df/dRe + i df/dIm) and objective."""
+    packed, t = _c128(packed), _c128(t)
+    i, j = _i32(i), _i32(j)
+    g = np.zeros_like(packed)
+    obj = ctypes.c_double(0.0)
+    _load().bfo_grad(n, L, b, r, lam, int(include_reg), _ptr(packed), len(i), _ptr(i),
+                     _ptr(j), _ptr(t), _ptr(g), ctypes.byref(obj))
+    return g, float(obj.value)
+
+
+def embed_lowrank(n, L, b, r, A, B, pad=None):
+    """Butterfly factors reproducing A B^T (A, B: n x R, R <= r)."""
+    A, B = _c128(A), _c128(B)
+    R = A.shape[1]
+    if pad is None:
+        pad = np.zeros((2 * n, max(r - R, 1)), dtype=np.complex128)
+    pad = _c128(pad)
+    out = np.zeros(num_params(n, L, b, r), dtype=np.complex128)
+    _load().bfo_embed_lowrank(n, L, b, r, R, _ptr(A), _ptr(B), _ptr(pad), _ptr(out))
+    return out
+
+
+def lr_complete(n, R, lam, A0, B0, i, j, t, sweeps):
+    """Low-rank matrix completion = Alg. 1 with L = 0 (leaf size n).
+    Returns (A, B) with X = A B^T."""
+    packed = np.concatenate([_c128(A0).ravel(), _c128(B0).ravel()])
+    for _ in range(sweeps):
+        packed, _st = als_sweep(n, 0, n, R, lam, packed, i, j, t)
+    return packed[:n * R].reshape(n, R), packed[n * R:].reshape(n, R)
