@@ -1,0 +1,218 @@
+/*
+ * bfc.h -- C ABI of the GB300 butterfly tensor completion library (libbfc.so).
+ *
+ * The operation: given an n x n complex matrix T observed on an index set
+ * Omega, find butterfly factors S = {S^1, ..., S^{L+2}} (n = b * 2^L, leaf
+ * size b, butterfly rank r) minimizing
+ *     f(S) = 1/2 sum_{(i,j) in Omega} |x_ij(S) - t_ij|^2 + lambda/2 ||S||^2,
+ * where x_ij(S) is the tensor-network entry formula Eq. (BF_tensor_rep),
+ * Sec. 3.1, and the objective is Eq. (BF_objective), Sec. 4, with the
+ * regularization of Sec. 4.1.1.  Alternating least squares follows Alg. 1.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Tree bits (Eq. (indices)): p_i = floor(i / b) is the L-bit tree prefix of
+ * row i with i_0 its most significant bit; i_L = i mod b.  Same for columns.
+ *
+ * Factor layout after the App. A.2 reshape (Eq. (reshaped_tensors)):
+ *   z1[i][a]            fiber s^1(i_0..i_L, :),           n x r
+ *   Z[m][k][a][c]       slice S^{m+1}(k, :, :), m = 1..L, k < 2^{L+1},
+ *                       k = psi^{-1}(i_0..i_{L-m}, j_0..j_{m-1}) MSB-first,
+ *                       i.e. k = ((p_i >> (m-1)) << m) | (p_j >> (L-m));
+ *                       a is the left rank index r_m, c the right one r_{m+1}
+ *   zL[j][c]            fiber s^{L+2}(j_0..j_L, :),       n x r
+ *   x_ij = z1[i]^T Z[1][k_2] ... Z[L][k_{L+1}] zL[j]   (no conjugation).
+ *
+ * "Packed" factor vectors are complex128, interleaved (re, im), of
+ * bfc_num_params() complex numbers: [ z1 : n r ][ Z : L 2^{L+1} r^2 ][ zL : n r ].
+ *
+ * Complex values (t, outputs) are always interleaved complex128 (2 doubles).
+ * Index arrays are int32.
+ *
+ * Ownership: the caller owns every array it passes; bfc_create copies the
+ * observed data to the device, so inputs may be freed after it returns.
+ * Output arrays are caller-allocated.  The context owns all device memory and
+ * releases it in bfc_destroy.  Pointers are host pointers unless
+ * params.values_on_device is 1, in which case the data arrays passed to
+ * bfc_create / bfc_set_factors / bfc_get_factors / bfc_eval / bfc_grad must
+ * be device pointers (for example from torch tensors).
+ *
+ * Errors: every call returns a bfc_status; no C++ exception crosses the ABI.
+ * bfc_last_error() gives a message for the last failing call on a context.
+ * Calls on one context are ordered on its stream (bfc_set_stream) and return
+ * after the stream work they issued has finished.  Use one context per host
+ * thread.
+ */
+#ifndef BFC_H
+#define BFC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bfc_ctx bfc_ctx;
+
+typedef enum {
+    BFC_OK = 0,
+    BFC_EINVAL = 1,      /* invalid argument: sizes, indices, duplicates, NaN/Inf */
+    BFC_ENOMEM = 2,      /* device or host allocation failed */
+    BFC_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    BFC_ESINGULAR = 4,   /* reserved: a solve could not proceed at all */
+    BFC_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+    BFC_ENONFINITE = 6   /* a result became NaN or Inf */
+} bfc_status;
+
+typedef enum {
+    /* Everything in FP64: environment chains, normal-equation sums, solves. */
+    BFC_PREC_FP64 = 0,
+    /* Precision form: chains and normal-equation sums in complex64 with
+     * compensated accumulation; per-slice solves and the factor master copy
+     * in FP64 (complex64 Cholesky with FP64 iterative refinement, FP64
+     * Cholesky fallback). */
+    BFC_PREC_C64_FP64SOLVE = 1
+} bfc_precision;
+
+typedef struct {
+    int64_t n;              /* matrix size; must equal b * 2^L               */
+    int32_t L;              /* butterfly levels, 0 <= L <= 24 (L = 0: low-rank) */
+    int32_t b;              /* leaf size (the paper's c), >= 1               */
+    int32_t r;              /* butterfly rank, 1 <= r <= 10                  */
+    double lambda;          /* regularization added to every system, >= 0    */
+    int32_t prec;           /* bfc_precision                                 */
+    int32_t max_sweeps;     /* bfc_complete: sweep limit                     */
+    double tol;             /* bfc_complete: stop when train rel. err < tol  */
+    uint64_t seed;          /* bfc_complete with init_kind 1: random start   */
+    int32_t init_kind;      /* bfc_complete: 0 = current factors,
+                               1 = low-rank completion (Alg. 1 with L = 0,
+                                   rank lr_rank, lr_sweeps sweeps) embedded
+                                   exactly into the butterfly              */
+    int32_t lr_rank;        /* rank R of the low-rank start (<= r)           */
+    int32_t lr_sweeps;      /* sweeps of low-rank completion                 */
+    int32_t values_on_device; /* 1: data pointers are device pointers        */
+    int32_t refine_sweeps;  /* precision form: FP64 sweeps appended by
+                               bfc_complete after the complex64 sweeps       */
+} bfc_params;
+
+typedef struct {
+    int32_t sweep;          /* 1-based sweep number                          */
+    double train_rel_err;   /* Eq. (BF_convergence) on the training set      */
+    double test_rel_err;    /* same on the test set (-1 if none)             */
+    double objective;       /* f(S) after the sweep                          */
+    double sweep_ms;        /* device time of the sweep (CUDA events)        */
+    double entries_per_s;   /* training entries / sweep time                 */
+    int64_t singular_slices;/* systems left unchanged (Cholesky breakdown)   */
+    int64_t refined_fallbacks; /* precision form: FP64 Cholesky fallbacks    */
+} bfc_sweep_stats;
+
+typedef struct {
+    char name[48];          /* kernel name                                   */
+    int64_t launches;       /* launches since profiling was enabled          */
+    double total_ms;        /* summed CUDA-event durations                   */
+} bfc_kernel_profile;
+
+/* Number of complex parameters 2 n r + L 2^{L+1} r^2 (Sec. 2.2 memory count
+ * with the App. A.2 reshape).  Returns -1 for invalid sizes. */
+int64_t bfc_num_params(int64_t n, int32_t L, int32_t b, int32_t r);
+
+/* Create a context for one completion problem (Sec. 4 problem statement:
+ * T on Omega, sizes, rank, lambda).  Copies the nnz training entries
+ * (i[e], j[e], t[e]) and ntest test entries (it, jt, tt; ntest may be 0) to
+ * the device, validates them (indices in [0, n), no duplicate (i, j) in the
+ * training set since Omega is a set, finite values), builds the per-factor
+ * entry orderings (the "transpose the sparse tensor according to the index
+ * being solved for" step of App. A.2) and zero-initializes the factors.
+ * On success *out receives the context; on failure *out is NULL.
+ * Errors: EINVAL (n != b 2^L, r out of range, lambda < 0, nnz <= 0,
+ * bad index, duplicate, NaN/Inf), ENOMEM, ECUDA. */
+bfc_status bfc_create(const bfc_params* params, int64_t nnz, const int32_t* i,
+                      const int32_t* j, const double* t, int64_t ntest,
+                      const int32_t* it, const int32_t* jt, const double* tt,
+                      bfc_ctx** out);
+
+/* Run all further work of this context on `cuda_stream` (a cudaStream_t;
+ * NULL selects the context's own stream). */
+bfc_status bfc_set_stream(bfc_ctx* ctx, void* cuda_stream);
+
+/* Replace the factors by a packed complex128 vector (layout above). */
+bfc_status bfc_set_factors(bfc_ctx* ctx, const double* packed);
+
+/* Copy the current factors (FP64 master copy) into a packed vector. */
+bfc_status bfc_get_factors(bfc_ctx* ctx, double* packed);
+
+/* Evaluate x_ij (Eq. (BF_tensor_rep)) for m index pairs; out receives m
+ * interleaved complex128 values.  Arithmetic follows the context precision
+ * (FP64, or complex64 chains in the precision form).  EINVAL on an index
+ * outside [0, n). */
+bfc_status bfc_eval(bfc_ctx* ctx, int64_t m, const int32_t* i, const int32_t* j,
+                    double* out);
+
+/* One ALS sweep (Alg. 1): S^1 fibers, then S^2 .. S^{L+1} slices in order,
+ * then S^{L+2} fibers, each block the exact minimizer of f with the newest
+ * values of all other factors (complex normal equations
+ * K = sum conj(a) a^T + lambda I, y = sum conj(a) t).  A system whose
+ * Cholesky pivot falls to <= 0 (<= 1e-14 trace(K) when lambda = 0) keeps its
+ * old values and is counted in singular_slices.  `out` may be NULL. */
+bfc_status bfc_als_sweep(bfc_ctx* ctx, bfc_sweep_stats* out);
+
+/* Gradient of f with respect to all parameters (Eqs. (grad_butterfly_1),
+ * (grad_butterfly_l), (grad_butterfly_last) with z = x - t), packed as
+ * df/dRe + i df/dIm; the regularization term lambda S is added when
+ * include_reg is nonzero.  grad_packed (may be NULL) receives the packed
+ * gradient, *objective (may be NULL) the value of f (with or without the
+ * regularization term, matching include_reg). */
+bfc_status bfc_grad(bfc_ctx* ctx, int32_t include_reg, double* grad_packed,
+                    double* objective);
+
+/* Low-rank start (Sec. 4.2): low-rank matrix completion of rank R <= r from
+ * the caller's starting factors A0, B0 (n x R packed complex128, X = A B^T),
+ * `sweeps` sweeps of Alg. 1 with L = 0 on the GPU, then the exact embedding
+ * z1 = A, every middle slice = identity, zL = B (columns R..r-1 zero).
+ * Sets the context's factors.  A0/B0 follow values_on_device. */
+bfc_status bfc_lowrank_init(bfc_ctx* ctx, int32_t R, int32_t sweeps,
+                            const double* A0, const double* B0);
+
+/* Full workflow (Sec. 4.3): optional low-rank start (init_kind 1, with a
+ * CN(0, sigma^2) SplitMix64 start from params.seed), then ALS sweeps until
+ * the training error (Eq. (BF_convergence)) is below params.tol or
+ * params.max_sweeps sweeps ran, then params.refine_sweeps FP64 sweeps in the
+ * precision form.  history (may be NULL) receives up to history_cap sweep
+ * records; *nsweeps (may be NULL) the number of sweeps run. */
+bfc_status bfc_complete(bfc_ctx* ctx, bfc_sweep_stats* history, int32_t history_cap,
+                        int32_t* nsweeps);
+
+/* Index decoding on the GPU (Eq. (indices) and the App. A.2 slice ids):
+ * for m host pairs (i[e], j[e]) writes keys[e * (L+2) + l] = i for l = 0, the
+ * slice id k_{l+1} of S^{l+1} for l = 1..L, and j for l = L+1.  These are
+ * the keys by which bfc_create orders the entries.  Host arrays; EINVAL on
+ * bad sizes or an index outside [0, n). */
+bfc_status bfc_decode(int64_t n, int32_t L, int32_t b, int64_t m, const int32_t* i,
+                      const int32_t* j, int32_t* keys);
+
+/* The entry ordering of one factor level (0 = S^1 rows, 1..L = slices of
+ * S^{l+1}, L+1 = S^{L+2} columns): perm[p] is the training entry (index into
+ * the arrays given to bfc_create) at position p, stable in input order within
+ * a key; seg[k] .. seg[k+1] is the range of key k (n + 1 values for levels 0
+ * and L+1, 2^{L+1} + 1 otherwise).  Host arrays; either may be NULL. */
+bfc_status bfc_get_order(bfc_ctx* ctx, int32_t level, int32_t* perm, int32_t* seg);
+
+/* Per-kernel device-time accounting with CUDA events on the context stream
+ * (off by default).  Enabling resets the counters. */
+bfc_status bfc_profile_enable(bfc_ctx* ctx, int32_t enable);
+/* Copy up to cap records; *count receives the number of distinct kernels. */
+bfc_status bfc_profile_read(bfc_ctx* ctx, bfc_kernel_profile* out, int32_t cap,
+                            int32_t* count);
+
+/* Message for the last failed call on ctx (or of the last failed
+ * bfc_create when ctx is NULL).  Never NULL. */
+const char* bfc_last_error(const bfc_ctx* ctx);
+
+/* Release the context and all its device memory.  NULL is ignored. */
+void bfc_destroy(bfc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFC_H */

@@ -1,0 +1,666 @@
+// C ABI of libbfc (include/bfc.h): context life cycle, data movement, the
+// sweep / gradient / completion drivers and per-kernel profiling.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "bfc_internal.h"
+#include "bfc_ops.h"
+#include "bfc_util.h"
+
+namespace bfc {
+
+static thread_local std::string g_create_err;
+
+bfc_status fail(Ctx* ctx, bfc_status st, const std::string& msg)
+{
+    if (ctx) ctx->err = msg;
+    else g_create_err = msg;
+    return st;
+}
+
+bfc_status dalloc(Ctx* c, void** p, size_t bytes, const char* what)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(c, e == cudaErrorMemoryAllocation ? BFC_ENOMEM : BFC_ECUDA,
+                    std::string("cudaMalloc(") + what + ", " + std::to_string(bytes) + " bytes): " +
+                        cudaGetErrorString(e));
+    }
+    c->allocs.push_back(*p);
+    return BFC_OK;
+}
+
+static void dfree(Ctx* c, void* p)
+{
+    if (!p) return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    cudaFree(p);
+}
+
+bfc_status ensure_tmp(Ctx* c, size_t bytes)
+{
+    if (bytes <= c->tmp_cap) return BFC_OK;
+    if (c->d_tmp) {
+        cudaStreamSynchronize(c->stream);
+        dfree(c, c->d_tmp);
+        c->d_tmp = nullptr;
+        c->tmp_cap = 0;
+    }
+    BFC_TRY(dalloc(c, &c->d_tmp, bytes, "scratch"));
+    c->tmp_cap = bytes;
+    return BFC_OK;
+}
+
+ProfScope::ProfScope(Ctx* ctx, const char* name) : c(ctx)
+{
+    if (!c->prof) return;
+    for (size_t q = 0; q < c->prof_rec.size(); ++q)
+        if (c->prof_rec[q].name == name) { rec = (int)q; break; }
+    if (rec < 0) {
+        c->prof_rec.push_back(ProfRecord{name, 0, 0.0});
+        rec = (int)c->prof_rec.size() - 1;
+    }
+    if (c->ev_pool.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { rec = -1; return; }
+        c->ev_pool.push_back(e);
+    }
+    a = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    cudaEventRecord(a, c->stream);
+}
+
+ProfScope::~ProfScope()
+{
+    if (rec < 0 || !a) return;
+    cudaEvent_t b;
+    if (c->ev_pool.empty()) {
+        if (cudaEventCreate(&b) != cudaSuccess) { c->ev_pool.push_back(a); return; }
+    } else {
+        b = c->ev_pool.back();
+        c->ev_pool.pop_back();
+    }
+    cudaEventRecord(b, c->stream);
+    c->prof_pending.push_back(ProfPending{rec, a, b});
+}
+
+void prof_collect(Ctx* c)
+{
+    if (c->prof_pending.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto& p : c->prof_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            c->prof_rec[p.rec].launches += 1;
+            c->prof_rec[p.rec].total_ms += ms;
+        }
+        c->ev_pool.push_back(p.a);
+        c->ev_pool.push_back(p.b);
+    }
+    c->prof_pending.clear();
+}
+
+// ------------------------------------------------------------------ helpers
+
+static bool valid_sizes(int64_t n, int L, int b, int r)
+{
+    if (L < 0 || L > 24 || b < 1 || r < 1 || r > MAX_RANK || n < 1) return false;
+    if (n != (int64_t)b << L) return false;
+    if (n > (int64_t)1 << 30) return false;
+    return true;
+}
+
+static bfc_status sync(Ctx* c)
+{
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, BFC_ECUDA, std::string("stream: ") + cudaGetErrorString(e));
+    prof_collect(c);
+    return BFC_OK;
+}
+
+static cudaMemcpyKind in_kind(const Ctx* c) { return c->P.values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+static cudaMemcpyKind out_kind(const Ctx* c) { return c->P.values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+// Refresh the compute-type copies of the factors from the FP64 masters.
+static bfc_status refresh_copies(Ctx* c)
+{
+    if (!c->fp32) return BFC_OK;
+    launch_d2f(c->z1d, (float2*)c->z1t, c->n * c->r, c->stream);
+    launch_d2f(c->Zd, (float2*)c->Zt, (int64_t)c->L * c->S * c->r * c->r, c->stream);
+    launch_d2f(c->zLd, (float2*)c->zLt, c->n * c->r, c->stream);
+    BFC_LAUNCH_CHECK(c, "d2f");
+    return BFC_OK;
+}
+
+// Sum of squares of the FP64 master factors into d_scalars[slot].
+static bfc_status factor_sumsq(Ctx* c, int slot)
+{
+    const int nb = (int)std::min<int64_t>(1216, (c->Pn + 255) / 256);
+    launch_sumsq(c->z1d, c->Pn, c->d_red, nb, c->stream);  // factors are contiguous (one allocation)
+    launch_reduce_single(c->d_red, nb, c->d_scalars + slot, c->stream);
+    BFC_LAUNCH_CHECK(c, "sumsq");
+    return BFC_OK;
+}
+
+// ------------------------------------------------------------------ create
+
+struct Inputs {
+    int64_t nnz;
+    const int32_t *i, *j;
+    const double* t;
+    int64_t ntest;
+    const int32_t *it, *jt;
+    const double* tt;
+    cudaMemcpyKind kind;
+};
+
+static bfc_status build(Ctx* c, const Inputs& in)
+{
+    const int64_t N = c->N, n = c->n, S = c->S;
+    const int L = c->L, r = c->r;
+    BFC_CK(c, cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    c->stream = c->own_stream;
+    BFC_CK(c, cudaEventCreate(&c->ev0));
+    BFC_CK(c, cudaEventCreate(&c->ev1));
+
+    BFC_TRY(dalloc(c, (void**)&c->d_i, N * 4, "i"));
+    BFC_TRY(dalloc(c, (void**)&c->d_j, N * 4, "j"));
+    BFC_TRY(dalloc(c, (void**)&c->d_t, N * 16, "t"));
+    BFC_CK(c, cudaMemcpyAsync(c->d_i, in.i, N * 4, in.kind, c->stream));
+    BFC_CK(c, cudaMemcpyAsync(c->d_j, in.j, N * 4, in.kind, c->stream));
+    BFC_CK(c, cudaMemcpyAsync(c->d_t, in.t, N * 16, in.kind, c->stream));
+    if (c->NT > 0) {
+        BFC_TRY(dalloc(c, (void**)&c->d_it, c->NT * 4, "it"));
+        BFC_TRY(dalloc(c, (void**)&c->d_jt, c->NT * 4, "jt"));
+        BFC_TRY(dalloc(c, (void**)&c->d_tt, c->NT * 16, "tt"));
+        BFC_CK(c, cudaMemcpyAsync(c->d_it, in.it, c->NT * 4, in.kind, c->stream));
+        BFC_CK(c, cudaMemcpyAsync(c->d_jt, in.jt, c->NT * 4, in.kind, c->stream));
+        BFC_CK(c, cudaMemcpyAsync(c->d_tt, in.tt, c->NT * 16, in.kind, c->stream));
+    }
+    BFC_TRY(dalloc(c, (void**)&c->d_scalars, 16 * sizeof(double), "scalars"));
+    BFC_TRY(dalloc(c, (void**)&c->d_count, 8 * sizeof(unsigned long long), "counters"));
+    c->red_cap = std::max<int64_t>(2 * n, 8192);
+    BFC_TRY(dalloc(c, (void**)&c->d_red, c->red_cap * sizeof(double), "reduction"));
+
+    // validation: index range, finite values
+    int* dflag = (int*)c->d_count;
+    BFC_CK(c, cudaMemsetAsync(dflag, 0, sizeof(int), c->stream));
+    launch_check_entries(c->d_i, c->d_j, c->d_t, N, n, dflag, c->stream);
+    launch_check_entries(c->d_it, c->d_jt, c->d_tt, c->NT, n, dflag, c->stream);
+    BFC_LAUNCH_CHECK(c, "check_entries");
+    int hflag = 0;
+    BFC_CK(c, cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BFC_TRY(sync(c));
+    if (hflag & 1) return fail(c, BFC_EINVAL, "an index is outside [0, n)");
+    if (hflag & 2) return fail(c, BFC_EINVAL, "a value is NaN or Inf");
+
+    // level orders
+    SortScratch ss;
+    const int64_t T = (N + RS_TILE - 1) / RS_TILE;
+    std::vector<void*> temps;
+    auto tmp = [&](void** p, size_t bytes, const char* w) -> bfc_status {
+        BFC_TRY(dalloc(c, p, bytes, w));
+        temps.push_back(*p);
+        return BFC_OK;
+    };
+    BFC_TRY(tmp((void**)&ss.k0, N * 4, "sort keys"));
+    BFC_TRY(tmp((void**)&ss.k1, N * 4, "sort keys"));
+    BFC_TRY(tmp((void**)&ss.v0, N * 4, "sort vals"));
+    BFC_TRY(tmp((void**)&ss.v1, N * 4, "sort vals"));
+    BFC_TRY(tmp((void**)&ss.counts, (size_t)256 * T * 4, "sort counts"));
+    const int NL = L + 2;
+    std::vector<int32_t*>& perm = c->perm;
+    std::vector<int32_t*> pos(NL);
+    perm.assign(NL, nullptr);
+    c->seg.assign(NL, nullptr);
+    c->tval.assign(NL, nullptr);
+    c->nxt.assign(L + 1, nullptr);
+    c->prv.assign(L + 1, nullptr);
+    for (int l = 0; l < NL; ++l) {
+        const int64_t K = (l == 0 || l == L + 1) ? n : S;
+        BFC_TRY(dalloc(c, (void**)&perm[l], N * 4, "perm"));
+        BFC_TRY(tmp((void**)&pos[l], N * 4, "pos"));
+        BFC_TRY(dalloc(c, (void**)&c->seg[l], (K + 1) * 4, "segments"));
+        BFC_TRY(dalloc(c, &c->tval[l], N * c->vsz, "level values"));
+        BFC_CK(c, sort_level(c->d_i, c->d_j, N, l, L, c->b, K, c->stream, ss, perm[l], c->seg[l]));
+        launch_invert(perm[l], N, pos[l], c->stream);
+        launch_gather_values(c->d_t, perm[l], N, c->tval[l], c->fp32, c->stream);
+        BFC_LAUNCH_CHECK(c, "prep");
+    }
+    // duplicates: columns within each row segment must be distinct
+    int32_t* jrow = ss.v1;  // free after the sorts
+    launch_gather_i32(c->d_j, perm[0], N, jrow, c->stream);
+    BFC_CK(c, cudaMemsetAsync(dflag, 0, sizeof(int), c->stream));
+    launch_row_dups(c->seg[0], jrow, n, dflag, c->stream);
+    BFC_LAUNCH_CHECK(c, "row_dups");
+    for (int l = 0; l <= L; ++l) {
+        BFC_TRY(dalloc(c, (void**)&c->nxt[l], N * 4, "nxt"));
+        launch_compose(perm[l], pos[l + 1], N, c->nxt[l], c->stream);
+        if (l >= 1) {
+            BFC_TRY(dalloc(c, (void**)&c->prv[l], N * 4, "prv"));
+            launch_compose(perm[l], pos[l - 1], N, c->prv[l], c->stream);
+        }
+    }
+    BFC_TRY(dalloc(c, (void**)&c->jL, N * 4, "jL"));
+    launch_gather_i32(c->d_j, perm[L], N, c->jL, c->stream);
+    BFC_LAUNCH_CHECK(c, "maps");
+    BFC_CK(c, cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BFC_TRY(sync(c));
+    for (void* p : temps) dfree(c, p);
+    if (hflag & 4) return fail(c, BFC_EINVAL, "duplicate (i, j) pair in the training set");
+
+    // environments
+    BFC_TRY(dalloc(c, &c->W, (size_t)(L + 1) * N * r * c->vsz, "right environments"));
+    for (int q = 0; q < 2; ++q) {
+        BFC_TRY(dalloc(c, &c->H[q], (size_t)N * r * c->vsz, "left environments"));
+        BFC_TRY(dalloc(c, &c->Rres[q], (size_t)N * c->vsz, "residuals"));
+    }
+    // factors: one allocation, FP64 master [z1 | Z | zL]
+    BFC_TRY(dalloc(c, (void**)&c->z1d, (size_t)c->Pn * 16, "factors"));
+    c->Zd = c->z1d + n * r;
+    c->zLd = c->Zd + (size_t)L * S * r * r;
+    BFC_CK(c, cudaMemsetAsync(c->z1d, 0, (size_t)c->Pn * 16, c->stream));
+    if (c->fp32) {
+        void* ft;
+        BFC_TRY(dalloc(c, &ft, (size_t)c->Pn * 8, "factors c64"));
+        c->z1t = ft;
+        c->Zt = (float2*)ft + n * r;
+        c->zLt = (float2*)c->Zt + (size_t)L * S * r * r;
+        BFC_CK(c, cudaMemsetAsync(ft, 0, (size_t)c->Pn * 8, c->stream));
+    } else {
+        c->z1t = c->z1d;
+        c->Zt = c->Zd;
+        c->zLt = c->zLd;
+    }
+    const Ops* ops = get_ops(c->fp32, r);
+    BFC_TRY(ops->configure(c));
+    return sync(c);
+}
+
+static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ctx** out)
+{
+    if (out) *out = nullptr;
+    if (!params || !out) return fail(nullptr, BFC_EINVAL, "null argument");
+    const bfc_params& p = *params;
+    if (!valid_sizes(p.n, p.L, p.b, p.r))
+        return fail(nullptr, BFC_EINVAL, "invalid sizes: need n = b * 2^L, 0 <= L <= 24, 1 <= r <= 10");
+    if (!(p.lambda >= 0.0) || !isfinite(p.lambda)) return fail(nullptr, BFC_EINVAL, "lambda must be finite and >= 0");
+    if (p.prec != BFC_PREC_FP64 && p.prec != BFC_PREC_C64_FP64SOLVE)
+        return fail(nullptr, BFC_EINVAL, "unknown precision");
+    if (in.nnz <= 0 || in.nnz >= ((int64_t)1 << 31) - 1) return fail(nullptr, BFC_EINVAL, "nnz must be in [1, 2^31-2]");
+    if (in.ntest < 0 || in.ntest >= ((int64_t)1 << 31) - 1) return fail(nullptr, BFC_EINVAL, "bad ntest");
+    if (!in.i || !in.j || !in.t) return fail(nullptr, BFC_EINVAL, "null training data");
+    if (in.ntest > 0 && (!in.it || !in.jt || !in.tt)) return fail(nullptr, BFC_EINVAL, "null test data");
+    Ctx* c = new Ctx();
+    c->P = p;
+    c->n = p.n;
+    c->L = p.L;
+    c->b = p.b;
+    c->r = p.r;
+    c->S = (int64_t)1 << (p.L + 1);
+    c->N = in.nnz;
+    c->NT = in.ntest;
+    c->Pn = bfc_num_params(p.n, p.L, p.b, p.r);
+    c->fp32 = p.prec == BFC_PREC_C64_FP64SOLVE;
+    c->vsz = c->fp32 ? 8 : 16;
+    bfc_status st = build(c, in);
+    if (st != BFC_OK) {
+        g_create_err = c->err;
+        bfc_destroy((bfc_ctx*)c);
+        return st;
+    }
+    *out = (bfc_ctx*)c;
+    return BFC_OK;
+}
+
+// ---------------------------------------------------------------- sweeps
+
+static bfc_status collect_stats(Ctx* c, bfc_sweep_stats* out, float ms)
+{
+    double hs[8];
+    unsigned long long hc[2];
+    BFC_CK(c, cudaMemcpyAsync(hs, c->d_scalars, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    BFC_CK(c, cudaMemcpyAsync(hc, c->d_count, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    BFC_TRY(sync(c));
+    if (out) {
+        out->sweep = c->sweeps_done;
+        out->train_rel_err = hs[1] > 0 ? sqrt(hs[0] / hs[1]) : sqrt(hs[0]);
+        out->test_rel_err = c->NT > 0 ? (hs[4] > 0 ? sqrt(hs[3] / hs[4]) : sqrt(hs[3])) : -1.0;
+        out->objective = 0.5 * hs[0] + 0.5 * c->P.lambda * hs[2];
+        out->sweep_ms = ms;
+        out->entries_per_s = ms > 0 ? (double)c->N / (ms * 1e-3) : 0.0;
+        out->singular_slices = (int64_t)hc[0];
+        out->refined_fallbacks = (int64_t)hc[1];
+    }
+    if (!isfinite(hs[0])) return fail(c, BFC_ENONFINITE, "training residual is not finite");
+    return BFC_OK;
+}
+
+static bfc_status test_error(Ctx* c, int slot)
+{
+    if (c->NT <= 0) return BFC_OK;
+    const Ops* ops = get_ops(c->fp32, c->r);
+    const int nb = (int)std::min<int64_t>(1216, (c->NT + 255) / 256);
+    BFC_TRY(ops->eval(c, c->d_it, c->d_jt, c->NT, nullptr, c->d_tt, c->d_red, nb));
+    launch_reduce_pairs(c->d_red, nb, c->d_scalars + slot, c->stream);
+    BFC_LAUNCH_CHECK(c, "reduce");
+    return BFC_OK;
+}
+
+static bfc_status sweep_impl(Ctx* c, bfc_sweep_stats* out)
+{
+    const Ops* ops = get_ops(c->fp32, c->r);
+    BFC_CK(c, cudaMemsetAsync(c->d_count, 0, 2 * sizeof(unsigned long long), c->stream));
+    BFC_CK(c, cudaEventRecord(c->ev0, c->stream));
+    BFC_TRY(ops->sweep(c));
+    BFC_TRY(factor_sumsq(c, 2));
+    BFC_TRY(test_error(c, 3));
+    BFC_CK(c, cudaEventRecord(c->ev1, c->stream));
+    c->sweeps_done += 1;
+    BFC_TRY(sync(c));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    return collect_stats(c, out, ms);
+}
+
+}  // namespace bfc
+
+using namespace bfc;
+
+// ==================================================================== ABI
+
+extern "C" {
+
+int64_t bfc_num_params(int64_t n, int32_t L, int32_t b, int32_t r)
+{
+    if (L < 0 || L > 24 || b < 1 || r < 1 || n != (int64_t)b << L) return -1;
+    return 2 * n * r + (int64_t)L * ((int64_t)1 << (L + 1)) * r * r;
+}
+
+bfc_status bfc_create(const bfc_params* params, int64_t nnz, const int32_t* i, const int32_t* j, const double* t,
+                      int64_t ntest, const int32_t* it, const int32_t* jt, const double* tt, bfc_ctx** out)
+{
+    Inputs in{nnz, i, j, t, ntest, it, jt, tt,
+              (params && params->values_on_device) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice};
+    return create_impl(params, in, out);
+}
+
+bfc_status bfc_set_stream(bfc_ctx* ctx, void* cuda_stream)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    BFC_TRY(sync(c));
+    c->stream = cuda_stream ? (cudaStream_t)cuda_stream : c->own_stream;
+    return BFC_OK;
+}
+
+bfc_status bfc_set_factors(bfc_ctx* ctx, const double* packed)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c || !packed) return c ? fail(c, BFC_EINVAL, "null factors") : BFC_EINVAL;
+    BFC_CK(c, cudaMemcpyAsync(c->z1d, packed, (size_t)c->Pn * 16, in_kind(c), c->stream));
+    BFC_TRY(refresh_copies(c));
+    return sync(c);
+}
+
+bfc_status bfc_get_factors(bfc_ctx* ctx, double* packed)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c || !packed) return c ? fail(c, BFC_EINVAL, "null output") : BFC_EINVAL;
+    BFC_CK(c, cudaMemcpyAsync(packed, c->z1d, (size_t)c->Pn * 16, out_kind(c), c->stream));
+    return sync(c);
+}
+
+bfc_status bfc_eval(bfc_ctx* ctx, int64_t m, const int32_t* i, const int32_t* j, double* out)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    if (m < 0 || (m > 0 && (!i || !j || !out))) return fail(c, BFC_EINVAL, "bad eval arguments");
+    if (m == 0) return BFC_OK;
+    const size_t ib = ((size_t)m * 4 + 255) / 256 * 256;
+    BFC_TRY(ensure_tmp(c, 2 * ib + (size_t)m * 16 + 256));
+    int32_t* di = (int32_t*)c->d_tmp;
+    int32_t* dj = (int32_t*)((char*)c->d_tmp + ib);
+    double2* dout = (double2*)((char*)c->d_tmp + 2 * ib);
+    BFC_CK(c, cudaMemcpyAsync(di, i, m * 4, in_kind(c), c->stream));
+    BFC_CK(c, cudaMemcpyAsync(dj, j, m * 4, in_kind(c), c->stream));
+    int* dflag = (int*)(c->d_count + 4);
+    BFC_CK(c, cudaMemsetAsync(dflag, 0, sizeof(int), c->stream));
+    launch_check_entries(di, dj, nullptr, m, c->n, dflag, c->stream);
+    int hflag = 0;
+    BFC_CK(c, cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BFC_TRY(sync(c));
+    if (hflag) return fail(c, BFC_EINVAL, "an index is outside [0, n)");
+    const Ops* ops = get_ops(c->fp32, c->r);
+    const int nb = (int)std::min<int64_t>(1216 * 4, (m + 255) / 256);
+    BFC_TRY(ops->eval(c, di, dj, m, dout, nullptr, nullptr, nb));
+    BFC_CK(c, cudaMemcpyAsync(out, dout, (size_t)m * 16, out_kind(c), c->stream));
+    return sync(c);
+}
+
+bfc_status bfc_als_sweep(bfc_ctx* ctx, bfc_sweep_stats* out)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    return sweep_impl(c, out);
+}
+
+bfc_status bfc_grad(bfc_ctx* ctx, int32_t include_reg, double* grad_packed, double* objective)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    const size_t gb = (size_t)c->Pn * 16;
+    BFC_TRY(ensure_tmp(c, gb + 256));
+    double2* G = (double2*)c->d_tmp;
+    double* part = c->d_red;  // n fiber partials
+    const Ops* ops = get_ops(c->fp32, c->r);
+    BFC_TRY(ops->grad(c, G, part));
+    launch_reduce_single(part, c->n, c->d_scalars + 0, c->stream);
+    BFC_TRY(factor_sumsq(c, 2));
+    if (include_reg) launch_axpy((double*)G, (const double*)c->z1d, c->P.lambda, 2 * c->Pn, c->stream);
+    BFC_LAUNCH_CHECK(c, "grad tail");
+    double hs[3];
+    BFC_CK(c, cudaMemcpyAsync(hs, c->d_scalars, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (grad_packed) BFC_CK(c, cudaMemcpyAsync(grad_packed, G, gb, out_kind(c), c->stream));
+    BFC_TRY(sync(c));
+    if (objective) *objective = 0.5 * hs[0] + (include_reg ? 0.5 * c->P.lambda * hs[2] : 0.0);
+    return BFC_OK;
+}
+
+bfc_status bfc_lowrank_init(bfc_ctx* ctx, int32_t R, int32_t sweeps, const double* A0, const double* B0)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    if (R < 1 || R > c->r || sweeps < 0 || !A0 || !B0) return fail(c, BFC_EINVAL, "bad low-rank arguments");
+    // Low-rank completion is Alg. 1 with L = 0 and leaf size n on the same data.
+    bfc_params lp = c->P;
+    lp.L = 0;
+    lp.b = (int32_t)c->n;
+    lp.r = R;
+    lp.values_on_device = 1;
+    Inputs in{c->N, c->d_i, c->d_j, (const double*)c->d_t, 0, nullptr, nullptr, nullptr, cudaMemcpyDeviceToDevice};
+    bfc_ctx* lr = nullptr;
+    bfc_status st = create_impl(&lp, in, &lr);
+    if (st != BFC_OK) return fail(c, st, std::string("low-rank context: ") + g_create_err);
+    Ctx* lc = (Ctx*)lr;
+    const size_t half = (size_t)c->n * R * 16;
+    cudaError_t e1 = cudaMemcpyAsync(lc->z1d, A0, half, in_kind(c), lc->stream);
+    cudaError_t e2 = cudaMemcpyAsync(lc->zLd, B0, half, in_kind(c), lc->stream);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        bfc_destroy(lr);
+        return fail(c, BFC_ECUDA, "copy of the low-rank start failed");
+    }
+    st = refresh_copies(lc);
+    for (int s = 0; s < sweeps && st == BFC_OK; ++s) st = sweep_impl(lc, nullptr);
+    if (st == BFC_OK) st = sync(lc);
+    if (st != BFC_OK) {
+        std::string m = lc->err;
+        bfc_destroy(lr);
+        return fail(c, st, "low-rank completion: " + m);
+    }
+    launch_embed(lc->z1d, lc->zLd, c->n, R, c->r, (int64_t)c->L * c->S, c->z1d, c->Zd, c->zLd, c->stream);
+    cudaError_t e = cudaGetLastError();
+    // the embedding reads lc's buffers on c->stream: finish before freeing lc
+    cudaStreamSynchronize(c->stream);
+    bfc_destroy(lr);
+    if (e != cudaSuccess) return fail(c, BFC_ECUDA, std::string("embed: ") + cudaGetErrorString(e));
+    BFC_TRY(refresh_copies(c));
+    return sync(c);
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) + Box-Muller CN(0, sigma^2) start, the
+// same published recipe as the seeded input generators.
+static void splitmix_cnormal(uint64_t seed, uint64_t& k, int64_t count, double sigma, std::vector<double>& out)
+{
+    auto next = [&](void) {
+        k += 1;
+        uint64_t z = seed + k * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto unif = [&](void) { return ((double)(next() >> 11) + 1.0) * (1.0 / 9007199254740992.0); };
+    const int64_t half = count;  // 2*count normals, Box-Muller pairs
+    std::vector<double> u1(half), u2(half);
+    for (int64_t q = 0; q < half; ++q) u1[q] = unif();
+    for (int64_t q = 0; q < half; ++q) u2[q] = unif();
+    out.resize(2 * count);
+    const double sc = sigma / sqrt(2.0);
+    for (int64_t q = 0; q < half; ++q) {
+        const double rad = sqrt(-2.0 * log(u1[q]));
+        out[2 * q] = rad * cos(2.0 * M_PI * u2[q]) * sc;
+        out[2 * q + 1] = rad * sin(2.0 * M_PI * u2[q]) * sc;
+    }
+}
+
+bfc_status bfc_complete(bfc_ctx* ctx, bfc_sweep_stats* history, int32_t history_cap, int32_t* nsweeps)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    if (nsweeps) *nsweeps = 0;
+    if (c->P.init_kind == 1) {
+        const int R = c->P.lr_rank > 0 ? c->P.lr_rank : c->r;
+        if (R > c->r) return fail(c, BFC_EINVAL, "lr_rank > r");
+        // rms of the training values
+        launch_sumsq(c->d_t, c->N, c->d_red, 1, c->stream);
+        double ss = 0.0;
+        BFC_CK(c, cudaMemcpyAsync(&ss, c->d_red, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        BFC_TRY(sync(c));
+        const double rms = sqrt(ss / (double)c->N);
+        const double sigma = sqrt(rms / R);
+        uint64_t k = 0;
+        std::vector<double> A, B;
+        splitmix_cnormal(c->P.seed, k, c->n * R, sigma, A);
+        splitmix_cnormal(c->P.seed, k, c->n * R, sigma, B);
+        const int32_t saved = c->P.values_on_device;
+        c->P.values_on_device = 0;
+        bfc_status st = bfc_lowrank_init(ctx, R, c->P.lr_sweeps, A.data(), B.data());
+        c->P.values_on_device = saved;
+        BFC_TRY(st);
+    }
+    int done = 0;
+    for (int s = 0; s < c->P.max_sweeps; ++s) {
+        bfc_sweep_stats st{};
+        BFC_TRY(sweep_impl(c, &st));
+        if (history && done < history_cap) history[done] = st;
+        ++done;
+        if (st.train_rel_err < c->P.tol) break;
+    }
+    if (nsweeps) *nsweeps = done;
+    return BFC_OK;
+}
+
+bfc_status bfc_decode(int64_t n, int32_t L, int32_t b, int64_t m, const int32_t* i, const int32_t* j,
+                      int32_t* keys)
+{
+    if (L < 0 || L > 24 || b < 1 || n != (int64_t)b << L || m < 0) return fail(nullptr, BFC_EINVAL, "bad sizes");
+    if (m == 0) return BFC_OK;
+    if (!i || !j || !keys) return fail(nullptr, BFC_EINVAL, "null argument");
+    for (int64_t e = 0; e < m; ++e)
+        if (i[e] < 0 || i[e] >= n || j[e] < 0 || j[e] >= n) return fail(nullptr, BFC_EINVAL, "index outside [0, n)");
+    const int NL = L + 2;
+    int32_t *di = nullptr, *dj = nullptr, *dk = nullptr;
+    cudaError_t e = cudaMalloc((void**)&di, m * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dj, m * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dk, (size_t)m * NL * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(di, i, m * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dj, j, m * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        launch_all_keys(di, dj, m, L, b, dk, 0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(keys, dk, (size_t)m * NL * 4, cudaMemcpyDeviceToHost);
+    cudaFree(di);
+    cudaFree(dj);
+    cudaFree(dk);
+    if (e != cudaSuccess) return fail(nullptr, BFC_ECUDA, std::string("decode: ") + cudaGetErrorString(e));
+    return BFC_OK;
+}
+
+bfc_status bfc_get_order(bfc_ctx* ctx, int32_t level, int32_t* perm, int32_t* seg)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    if (level < 0 || level > c->L + 1) return fail(c, BFC_EINVAL, "level outside [0, L+1]");
+    const int64_t K = (level == 0 || level == c->L + 1) ? c->n : c->S;
+    if (perm) BFC_CK(c, cudaMemcpyAsync(perm, c->perm[level], c->N * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (seg) BFC_CK(c, cudaMemcpyAsync(seg, c->seg[level], (K + 1) * 4, cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+bfc_status bfc_profile_enable(bfc_ctx* ctx, int32_t enable)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    BFC_TRY(sync(c));
+    c->prof = enable != 0;
+    c->prof_rec.clear();
+    return BFC_OK;
+}
+
+bfc_status bfc_profile_read(bfc_ctx* ctx, bfc_kernel_profile* out, int32_t cap, int32_t* count)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    BFC_TRY(sync(c));
+    if (count) *count = (int32_t)c->prof_rec.size();
+    for (int q = 0; q < cap && q < (int)c->prof_rec.size(); ++q) {
+        memset(out[q].name, 0, sizeof(out[q].name));
+        strncpy(out[q].name, c->prof_rec[q].name.c_str(), sizeof(out[q].name) - 1);
+        out[q].launches = c->prof_rec[q].launches;
+        out[q].total_ms = c->prof_rec[q].total_ms;
+    }
+    return BFC_OK;
+}
+
+const char* bfc_last_error(const bfc_ctx* ctx)
+{
+    const Ctx* c = (const Ctx*)ctx;
+    return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+void bfc_destroy(bfc_ctx* ctx)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return;
+    if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+    if (c->stream && c->stream != c->own_stream) cudaStreamSynchronize(c->stream);
+    for (void* p : c->allocs) cudaFree(p);
+    for (auto& p : c->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,18 @@
+// Instantiation of the hot-path drivers for compute type float, ranks 1..5.
+#include "bfc_ops.h"
+#include "bfc_path.cuh"
+
+namespace bfc {
+
+template <typename T, int R> static Ops make_ops()
+{
+    return Ops{&Path<T, R>::configure, &Path<T, R>::sweep, &Path<T, R>::grad, &Path<T, R>::eval};
+}
+
+const Ops* ops_float_lo(int r)
+{
+    static const Ops tab[] = {make_ops<float, 1>(), make_ops<float, 2>(), make_ops<float, 3>(), make_ops<float, 4>(), make_ops<float, 5>(), };
+    return (r >= 1 && r <= 5) ? &tab[r - 1] : nullptr;
+}
+
+}  // namespace bfc

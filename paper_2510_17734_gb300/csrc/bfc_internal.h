@@ -1,0 +1,121 @@
+// Internal definitions of libbfc: the context object and host-side helpers.
+// Not part of the ABI (include/bfc.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bfc.h"
+
+namespace bfc {
+
+// Per-kernel CUDA-event accounting (bfc_profile_enable / bfc_profile_read).
+struct ProfRecord {
+    std::string name;
+    int64_t launches = 0;
+    double total_ms = 0.0;
+};
+struct ProfPending {
+    int rec;
+    cudaEvent_t a, b;
+};
+
+struct Ctx;
+bfc_status fail(Ctx* ctx, bfc_status st, const std::string& msg);
+
+// Device buffers of one completion problem.  Level l = 0 is the S^1 (row)
+// ordering of the training entries, l = 1..L the slice ordering of the middle
+// factor S^{l+1}, l = L+1 the S^{L+2} (column) ordering.
+struct Ctx {
+    bfc_params P{};
+    int64_t n = 0, N = 0, NT = 0, S = 0, Pn = 0;  // Pn: complex parameter count
+    int L = 0, b = 0, r = 0;
+    bool fp32 = false;              // compute type float (precision form) or double
+    size_t vsz = 16;                // bytes of one complex compute value
+    cudaStream_t stream = nullptr, own_stream = nullptr;
+    std::string err;
+
+    // observed data, original order
+    int32_t *d_i = nullptr, *d_j = nullptr;
+    double2* d_t = nullptr;
+    int32_t *d_it = nullptr, *d_jt = nullptr;
+    double2* d_tt = nullptr;
+
+    // orderings (built once per Omega)
+    std::vector<int32_t*> seg;   // L+2 segment offset arrays
+    std::vector<void*> tval;     // L+2 value arrays in level order (compute type)
+    std::vector<int32_t*> nxt;   // l = 0..L : position in order l+1 of the entry at position p of order l
+    std::vector<int32_t*> prv;   // l = 1..L : position in order l-1 (index 0 unused)
+    int32_t* jL = nullptr;       // column index of the entries in order L
+    std::vector<int32_t*> perm;  // L+2: entry index at each position of order l
+
+    // environments (compute type): W[l] (l = 0..L) in order l, two H buffers
+    void* W = nullptr;
+    void* H[2] = {nullptr, nullptr};
+    void* Rres[2] = {nullptr, nullptr};  // residual carried along the orders (gradient)
+
+    // factors: FP64 master and compute-type copies (alias when double)
+    double2 *z1d = nullptr, *Zd = nullptr, *zLd = nullptr;
+    void *z1t = nullptr, *Zt = nullptr, *zLt = nullptr;
+
+    // small device scratch: reductions and counters
+    double* d_red = nullptr;          // partial sums, size red_cap
+    int64_t red_cap = 0;
+    double* d_scalars = nullptr;      // 16 doubles of results
+    unsigned long long* d_count = nullptr;  // 8 counters
+    void* d_tmp = nullptr;            // growable scratch (eval inputs, etc.)
+    size_t tmp_cap = 0;
+
+    // sweep bookkeeping
+    int32_t sweeps_done = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    // profiling
+    bool prof = false;
+    std::vector<ProfRecord> prof_rec;
+    std::vector<ProfPending> prof_pending;
+    std::vector<cudaEvent_t> ev_pool;
+
+    std::vector<void*> allocs;        // everything cudaMalloc'ed by this context
+};
+
+// Allocation helper: records the pointer for bfc_destroy.
+bfc_status dalloc(Ctx* c, void** p, size_t bytes, const char* what);
+bfc_status ensure_tmp(Ctx* c, size_t bytes);
+
+// Profiling scope around one launch.
+struct ProfScope {
+    Ctx* c;
+    int rec = -1;
+    cudaEvent_t a = nullptr;
+    ProfScope(Ctx* ctx, const char* name);
+    ~ProfScope();
+};
+void prof_collect(Ctx* c);
+
+}  // namespace bfc
+
+#define BFC_CK(ctx, call)                                                          \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            return ::bfc::fail((ctx), BFC_ECUDA,                                   \
+                               std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define BFC_LAUNCH_CHECK(ctx, name)                                                 \
+    do {                                                                            \
+        cudaError_t e_ = cudaGetLastError();                                        \
+        if (e_ != cudaSuccess)                                                      \
+            return ::bfc::fail((ctx), BFC_ECUDA,                                    \
+                               std::string("launch ") + (name) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define BFC_TRY(call)                        \
+    do {                                     \
+        bfc_status s_ = (call);              \
+        if (s_ != BFC_OK) return s_;         \
+    } while (0)

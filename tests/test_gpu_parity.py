@@ -1,0 +1,312 @@
+"""Parity of the CUDA path (through the C ABI) with the complex128 oracle.
+
+Tolerances (from the precision of each path): integer work (decoding, entry
+orderings) bit-exact; FP64 path 1e-10 relative on entry values and the
+objective; complex64 precision form 1e-4 relative.  Relative deviations of
+entry values are measured against max(|x_ref|, rms(x_ref)) so that entries
+near zero do not dominate.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2510_17734_gb300 as bfc
+import synth
+from helpers import (block_objective, envs_numpy, level_keys, lstsq_block, rel_dev,
+                     split_packed)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {bfc.PREC_FP64: 1e-10, bfc.PREC_C64: 1e-4}
+PRECS = [bfc.PREC_FP64, bfc.PREC_C64]
+
+
+def lr_start(p, sweeps=10):
+    A, B = synth.random_lowrank_start(p, p.r)
+    A, B = oracle.lr_complete(p.n, p.r, p.lam, A, B, p.i, p.j, p.t, sweeps)
+    return oracle.embed_lowrank(p.n, p.L, p.b, p.r, A, B)
+
+
+def make(p, prec, **kw):
+    return bfc.Completion(p.n, p.L, p.b, p.r, p.lam, p.i, p.j, p.t, p.it, p.jt, p.tt, prec=prec, **kw)
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    p = synth.config(1)
+    return p, lr_start(p)
+
+
+@pytest.fixture(scope="module")
+def cfg2s():
+    # the n = 4096 workload's structure (b = 16, r = 6, 6 n log2 n samples,
+    # noise) at n = 1024 so the oracle finishes in seconds
+    p = synth.config(2, n_override=1024)
+    return p, lr_start(p)
+
+
+# ------------------------------------------------------------- integers
+
+def test_decode_bit_exact_exhaustive_small():
+    for (n, L, b) in [(64, 4, 4), (48, 4, 3), (32, 0, 32), (16, 4, 1)]:
+        i, j = synth.random_pairs_full(n)
+        keys = bfc.bfc_decode(n, L, b, i, j)
+        for e in range(0, len(i), 7):
+            want = [int(i[e])] + [oracle.slice_id(i[e], j[e], m, L, b) for m in range(1, L + 1)] + [int(j[e])]
+            assert list(keys[e]) == want
+
+
+def test_decode_bit_exact_large_sample():
+    n, L, b = 65536, 12, 16
+    i, j = synth.draw_pairs(n, 3000, 17)
+    keys = bfc.bfc_decode(n, L, b, i, j)
+    for e in range(len(i)):
+        want = [int(i[e])] + [oracle.slice_id(i[e], j[e], m, L, b) for m in range(1, L + 1)] + [int(j[e])]
+        assert list(keys[e]) == want
+
+
+def test_orders_are_stable_sorts(cfg1):
+    p, X0 = cfg1
+    with make(p, bfc.PREC_C64) as c:
+        for level in range(p.L + 2):
+            if level == 0:
+                key = p.i.astype(np.int64)
+            elif level == p.L + 1:
+                key = p.j.astype(np.int64)
+            else:
+                key = np.array([oracle.slice_id(a, b_, level, p.L, p.b) for a, b_ in zip(p.i, p.j)])
+            perm, seg = c.order(level)
+            np.testing.assert_array_equal(perm, np.argsort(key, kind="stable"))
+            K = p.n if level in (0, p.L + 1) else 1 << (p.L + 1)
+            np.testing.assert_array_equal(seg, np.searchsorted(np.sort(key), np.arange(K + 1)))
+
+
+# ------------------------------------------------------------------ eval
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_eval_parity(cfg2s, prec):
+    p, _ = cfg2s
+    X = synth.random_factors(p.n, p.L, p.r, 5)
+    with make(p, prec) as c:
+        c.set_factors(X)
+        np.testing.assert_array_equal(c.get_factors(), X)
+        got = c.eval(p.i, p.j)
+    want = oracle.eval_entries(p.n, p.L, p.b, p.r, X, p.i, p.j)
+    assert rel_dev(got, want) <= TOL[prec]
+
+
+# ------------------------------------------------------------- ALS sweep
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("which", ["cfg1", "cfg2s"])
+def test_one_sweep_parity(request, which, prec):
+    p, X0 = request.getfixturevalue(which)
+    Xo, st_o = oracle.als_sweep(p.n, p.L, p.b, p.r, p.lam, X0, p.i, p.j, p.t)
+    with make(p, prec) as c:
+        c.set_factors(X0)
+        st = c.sweep()
+        Xg = c.get_factors()
+    tol = TOL[prec]
+    assert abs(st["objective"] - st_o["objective"]) <= tol * abs(st_o["objective"])
+    assert abs(st["train_rel_err"] - st_o["train_rel_err"]) <= tol * st_o["train_rel_err"]
+    te_o = oracle.rel_err(p.n, p.L, p.b, p.r, Xo, p.it, p.jt, p.tt)
+    assert abs(st["test_rel_err"] - te_o) <= tol * te_o
+    assert st["singular_slices"] == st_o["singular"] == 0
+    # entries of the two results agree on both the training and test sets
+    for (ii, jj) in [(p.i, p.j), (p.it, p.jt)]:
+        xg = oracle.eval_entries(p.n, p.L, p.b, p.r, Xg, ii, jj)
+        xo = oracle.eval_entries(p.n, p.L, p.b, p.r, Xo, ii, jj)
+        assert rel_dev(xg, xo) <= 10 * tol
+    if prec == bfc.PREC_FP64:
+        # with lambda > 0 every block is strictly convex: the factors are unique
+        assert rel_dev(Xg, Xo) <= 1e-7
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ten_sweeps_cfg1_final_test_error(cfg1, prec):
+    p, X0 = cfg1
+    Xo = X0
+    for _ in range(p.sweeps):
+        Xo, _ = oracle.als_sweep(p.n, p.L, p.b, p.r, p.lam, Xo, p.i, p.j, p.t)
+    te_o = oracle.rel_err(p.n, p.L, p.b, p.r, Xo, p.it, p.jt, p.tt)
+    with make(p, prec) as c:
+        c.set_factors(X0)
+        hist = [c.sweep() for _ in range(p.sweeps)]
+    assert abs(hist[-1]["test_rel_err"] - te_o) <= 1e-4
+    objs = [h["objective"] for h in hist]
+    assert all(b_ <= a_ * (1 + 1e-6) for a_, b_ in zip(objs[:-1], objs[1:]))
+
+
+# -------------------------------------------------------------- gradient
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("include_reg", [True, False])
+def test_grad_parity(cfg2s, prec, include_reg):
+    p, X0 = cfg2s
+    go, fo = oracle.grad(p.n, p.L, p.b, p.r, p.lam, X0, p.i, p.j, p.t, include_reg=include_reg)
+    with make(p, prec) as c:
+        c.set_factors(X0)
+        gg, fg = c.grad(include_reg)
+    assert abs(fg - fo) <= TOL[prec] * abs(fo)
+    scale = np.abs(go).max()
+    assert np.abs(gg - go).max() <= TOL[prec] * 10 * scale
+
+
+# ------------------------------------------------------------ init paths
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_lowrank_init_parity(cfg1, prec):
+    p, _ = cfg1
+    A0, B0 = synth.random_lowrank_start(p, p.r)
+    A, B = oracle.lr_complete(p.n, p.r, p.lam, A0, B0, p.i, p.j, p.t, 10)
+    Xo = oracle.embed_lowrank(p.n, p.L, p.b, p.r, A, B)
+    with make(p, prec) as c:
+        c.lowrank_init(A0, B0, 10)
+        Xg = c.get_factors()
+    for (ii, jj) in [(p.i, p.j), (p.it, p.jt)]:
+        xg = oracle.eval_entries(p.n, p.L, p.b, p.r, Xg, ii, jj)
+        xo = oracle.eval_entries(p.n, p.L, p.b, p.r, Xo, ii, jj)
+        assert rel_dev(xg, xo) <= 100 * TOL[prec]
+
+
+def test_complete_matches_oracle_workflow(cfg1):
+    p, _ = cfg1
+    A0, B0 = synth.random_lowrank_start(p, p.r)   # same SplitMix64 recipe as the library's
+    A, B = oracle.lr_complete(p.n, p.r, p.lam, A0, B0, p.i, p.j, p.t, 10)
+    Xo = oracle.embed_lowrank(p.n, p.L, p.b, p.r, A, B)
+    for _ in range(p.sweeps):
+        Xo, st_o = oracle.als_sweep(p.n, p.L, p.b, p.r, p.lam, Xo, p.i, p.j, p.t)
+    te_o = oracle.rel_err(p.n, p.L, p.b, p.r, Xo, p.it, p.jt, p.tt)
+    with make(p, bfc.PREC_FP64, max_sweeps=p.sweeps, tol=0.0, seed=p.seed + synth.SEED_INIT,
+              init_kind=1, lr_rank=p.r, lr_sweeps=10) as c:
+        hist = c.complete()
+    assert len(hist) == p.sweeps
+    assert abs(hist[-1]["test_rel_err"] - te_o) <= 1e-6
+
+
+def test_complete_stops_at_tolerance(cfg1):
+    p, X0 = cfg1
+    with make(p, bfc.PREC_C64, max_sweeps=30, tol=5e-3) as c:
+        c.set_factors(X0)
+        hist = c.complete()
+    assert hist[-1]["train_rel_err"] < 5e-3
+    assert all(h["train_rel_err"] >= 5e-3 for h in hist[:-1])
+
+
+# ------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,L,b,r", [(48, 0, 48, 3), (24, 3, 3, 2), (64, 5, 2, 1), (96, 4, 6, 5),
+                                     (128, 3, 16, 7)])
+def test_odd_shapes_one_sweep(prec, n, L, b, r):
+    # leaf sizes that are not powers of two, L = 0 (low-rank), rank 1, ragged
+    # and empty slices (few observations)
+    X0 = synth.random_factors(n, L, r, 3 + n)
+    i, j = synth.draw_pairs(n, min(n * n, 6 * n * max(1, L) + 11), 8 + n)
+    t = synth.helmholtz_line(n, math.pi * n / 8, 1.0, i, j)
+    lam = 1e-6
+    Xo, st_o = oracle.als_sweep(n, L, b, r, lam, X0, i, j, t)
+    with bfc.Completion(n, L, b, r, lam, i, j, t, prec=prec) as c:
+        c.set_factors(X0)
+        st = c.sweep()
+        Xg = c.get_factors()
+    assert abs(st["objective"] - st_o["objective"]) <= 10 * TOL[prec] * abs(st_o["objective"])
+    xg = oracle.eval_entries(n, L, b, r, Xg, i, j)
+    xo = oracle.eval_entries(n, L, b, r, Xo, i, j)
+    assert rel_dev(xg, xo) <= 100 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_singular_fiber_kept_and_counted(prec):
+    n, L, b, r = 16, 1, 8, 2
+    X0 = synth.random_factors(n, L, r, 3)
+    i, j = synth.draw_pairs(n, 200, 5)
+    keep = i != 3
+    i, j = i[keep], j[keep]
+    t = synth.helmholtz_line(n, 10.0, 1.0, i, j)
+    _, st_o = oracle.als_sweep(n, L, b, r, 0.0, X0, i, j, t)
+    with bfc.Completion(n, L, b, r, 0.0, i, j, t, prec=prec) as c:
+        c.set_factors(X0)
+        st = c.sweep()
+        Xg = c.get_factors()
+    assert st["singular_slices"] == st_o["singular"] >= 1
+    np.testing.assert_array_equal(Xg[3 * r:4 * r], X0[3 * r:4 * r])
+
+
+def test_invalid_inputs_rejected():
+    n, L, b, r = 64, 2, 16, 2
+    i, j = synth.draw_pairs(n, 100, 1)
+    t = synth.helmholtz_line(n, 5.0, 1.0, i, j)
+    with pytest.raises(bfc.BfcError, match="EINVAL"):
+        bfc.Completion(n, L, 8, r, 1e-6, i, j, t)             # n != b 2^L
+    with pytest.raises(bfc.BfcError, match="EINVAL"):
+        bfc.Completion(n, L, b, 11, 1e-6, i, j, t)            # rank too large
+    with pytest.raises(bfc.BfcError, match="EINVAL"):
+        bfc.Completion(n, L, b, r, -1.0, i, j, t)             # lambda < 0
+    bad = i.copy()
+    bad[7] = n
+    with pytest.raises(bfc.BfcError, match="outside"):
+        bfc.Completion(n, L, b, r, 1e-6, bad, j, t)
+    dup_i = np.concatenate([i, i[:1]])
+    dup_j = np.concatenate([j, j[:1]])
+    with pytest.raises(bfc.BfcError, match="duplicate"):
+        bfc.Completion(n, L, b, r, 1e-6, dup_i, dup_j, np.concatenate([t, t[:1]]))
+    tn = t.copy()
+    tn[3] = np.nan
+    with pytest.raises(bfc.BfcError, match="NaN"):
+        bfc.Completion(n, L, b, r, 1e-6, i, j, tn)
+    with bfc.Completion(n, L, b, r, 1e-6, i, j, t) as c:
+        with pytest.raises(bfc.BfcError, match="outside"):
+            c.eval(np.array([0, -1]), np.array([0, 0]))
+
+
+# ------------------------------------------------- full size (n = 65536)
+
+@pytest.fixture(scope="module")
+def cfg3():
+    p = synth.config(3)
+    with bfc.Completion(p.n, p.L, p.b, p.r, p.lam, p.i, p.j, p.t, p.it, p.jt, p.tt,
+                        prec=bfc.PREC_C64) as c:
+        A0, B0 = synth.random_lowrank_start(p, p.r)
+        c.lowrank_init(A0, B0, 10)
+        X0 = c.get_factors()
+        s1 = c.sweep()
+        X1 = c.get_factors()
+        s2 = c.sweep()
+    return p, X0, X1, s1, s2
+
+
+def test_full_size_reported_errors_match_oracle(cfg3):
+    p, X0, X1, s1, s2 = cfg3
+    tr = oracle.rel_err(p.n, p.L, p.b, p.r, X1, p.i, p.j, p.t)
+    te = oracle.rel_err(p.n, p.L, p.b, p.r, X1, p.it, p.jt, p.tt)
+    assert abs(s1["train_rel_err"] - tr) <= 1e-4 * tr
+    assert abs(s1["test_rel_err"] - te) <= 1e-4 * te
+    assert s2["objective"] <= s1["objective"] * (1 + 1e-5)
+    assert s1["singular_slices"] == 0
+
+
+def test_full_size_sampled_blocks_are_optimal(cfg3):
+    # For sampled slices of every middle level, the GPU's new slice minimizes
+    # that slice's regularized least-squares problem (design vectors rebuilt
+    # here from the factors before and after the sweep).
+    p, X0, X1, s1, s2 = cfg3
+    z1o, Zo, zLo = split_packed(X0, p.n, p.L, p.b, p.r)
+    z1n, Zn, zLn = split_packed(X1, p.n, p.L, p.b, p.r)
+    keys = level_keys(p.i, p.j, p.L, p.b)
+    rng = np.random.default_rng(0)
+    for m in range(1, p.L + 1):
+        for k in rng.choice(1 << (p.L + 1), 2, replace=False):
+            sel = np.nonzero(keys[m - 1] == k)[0]
+            if sel.size == 0:
+                continue
+            Zmix = np.concatenate([Zn[: m - 1], Zo[m - 1:]])
+            h_new, _ = envs_numpy(z1n, Zmix, zLo, p.i[sel], p.j[sel], p.L, p.b, p.r)
+            _, w_o = envs_numpy(z1o, Zo, zLo, p.i[sel], p.j[sel], p.L, p.b, p.r)
+            A = np.einsum("ea,ec->eac", h_new[m], w_o[m]).reshape(sel.size, p.r * p.r)
+            s_opt = lstsq_block(A, p.t[sel], p.lam)
+            f_opt = block_objective(A, p.t[sel], p.lam, s_opt)
+            f_gpu = block_objective(A, p.t[sel], p.lam, Zn[m - 1, k].ravel())
+            assert f_gpu <= f_opt * (1 + 1e-4) + 1e-12

@@ -26,19 +26,7 @@ import synth
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-# ---------------------------------------------------------------- helpers
-# (the test's own reading of the packed layout, built from numpy reshapes)
-
-def split_packed(packed, n, L, b, r):
-    S = 1 << (L + 1)
-    z1 = packed[: n * r].reshape(n, r)
-    Z = packed[n * r: n * r + L * S * r * r].reshape(L, S, r, r)
-    zL = packed[n * r + L * S * r * r:].reshape(n, r)
-    return z1, Z, zL
-
-
-def join_packed(z1, Z, zL):
-    return np.concatenate([z1.ravel(), Z.ravel(), zL.ravel()])
+from helpers import envs_numpy, join_packed, lstsq_block, split_packed  # noqa: E402
 
 
 def dense_by_einsum(packed, n, L, b, r):
@@ -212,35 +200,6 @@ def test_gauge_invariance_every_bond():
 
 
 # ------------------------------------------------------------------- ALS
-
-def envs_numpy(z1, Z, zL, i, j, L, b, r):
-    """Left envs h_m (m=1..L+1) and right envs w_m (m=0..L) per entry, by the
-    test's own tensor indexing (numpy reshape of the App. A.2 layout)."""
-    N = len(i)
-    pi, pj = i // b, j // b
-    Zt = [Z[m].reshape((2,) * (L + 1) + (r, r)) for m in range(L)]
-
-    def slice_mats(m):
-        ib = [(pi >> (L - 1 - q)) & 1 for q in range(L)]
-        jb = [(pj >> (L - 1 - q)) & 1 for q in range(L)]
-        idx = tuple(ib[: L - m + 1]) + tuple(jb[:m])
-        return Zt[m - 1][idx]            # (N, r, r)
-
-    h = {1: z1[i]}
-    for m in range(1, L + 1):
-        h[m + 1] = np.einsum("ea,eac->ec", h[m], slice_mats(m))
-    w = {L: zL[j]}
-    for m in range(L, 0, -1):
-        w[m - 1] = np.einsum("eac,ec->ea", slice_mats(m), w[m])
-    return h, w
-
-
-def lstsq_block(A, t, lam):
-    d = A.shape[1]
-    Aa = np.vstack([A, math.sqrt(lam) * np.eye(d)])
-    ta = np.concatenate([t, np.zeros(d)])
-    return np.linalg.lstsq(Aa, ta, rcond=None)[0]
-
 
 def test_every_als_block_is_the_exact_regularized_lstsq():
     n, L, b, r = 64, 3, 8, 2
