@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark: ALS sweep entries/s for butterfly completion on one GB300.
+
+Workload (the n = 65536 precision-form problem): n = 65536, L = 12, b = 16,
+r = 8, omega = pi n / 16, receiver line at h = 1.5, |Omega| = 4 n log2 n
+(3,774,874 training / 419,430 test entries), lambda = 1e-7, complex64 chains
+with compensated normal-equation sums and FP64 per-slice solves.  Inputs are
+seeded synthetic data (synth.config(3)); the start is the low-rank completion
+start (Sec. 4.2) computed on the GPU.
+
+A step is one full ALS sweep (Alg. 1: right environments, S^1 fibers, the L
+middle factors, S^{L+2} fibers, training / test error and objective).  The
+working set (about 4.5 GB of environments, values and orders) is far larger
+than L2, so no flush is needed between steps.
+
+Lines printed (one JSON line, rank 0):
+  value      entries/s of the timed sweeps, whole job (sum over ranks)
+  e2e        the same through the public API with host buffers: every step
+             copies the factors from pinned host memory, sweeps, and copies
+             the factors and statistics back
+  roofline   dominant kernel (the per-slice normal-equation kernel)
+  cpu_baseline  the complex128 oracle timed on a bounded sample (rank 0)
+Multi-GPU: every rank runs an independent replica (the single problem does
+not shard without an exchange step); value is the sum over ranks.
+
+--impl reference times the oracle as it stands on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ALS sweep entries/s (n=65536 precision form)"
+UNIT = "entries/s"
+WORKLOAD = ("n=65536 L=12 b=16 r=8, exp(i w rho)/rho line-to-line kernel, w=pi n/16, h=1.5, "
+            "|Omega|=4 n log2 n (3774874 train / 419430 test), lambda=1e-7")
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ helpers
+
+def als_flops_per_entry(r: int) -> int:
+    """Algorithmic flops of one middle-level update per entry (Alg. 1):
+    Hermitian Gram r^2(r^2+1)/2 + right-hand side r^2 complex multiply-adds,
+    8 real flops each."""
+    return 8 * (r * r * (r * r + 1) // 2 + r * r)
+
+
+def lowrank_start(prob, bfc_mod, prec):
+    import synth
+    A0, B0 = synth.random_lowrank_start(prob, prob.r)
+    c = bfc_mod.Completion(prob.n, prob.L, prob.b, prob.r, prob.lam, prob.i, prob.j, prob.t,
+                           prob.it, prob.jt, prob.tt, prec=prec)
+    c.lowrank_init(A0, B0, 10)
+    return c
+
+
+def oracle_sample(prob, frac_every: int):
+    """Every `frac_every`-th training entry of the workload."""
+    sel = np.arange(0, prob.nnz, frac_every)
+    return prob.i[sel], prob.j[sel], prob.t[sel]
+
+
+def time_oracle_sweep(prob, X0, frac_every: int):
+    import oracle
+    i, j, t = oracle_sample(prob, frac_every)
+    t0 = time.perf_counter()
+    oracle.als_sweep(prob.n, prob.L, prob.b, prob.r, prob.lam, X0, i, j, t)
+    dt = time.perf_counter() - t0
+    return len(i), dt
+
+
+def oracle_full_rate(prob, m1, t1, m2, t2):
+    """Fit t = a + b m to two sampled sweeps (a: the per-slice and per-fiber
+    solves, which a sample keeps in full; b: per-entry work) and return the
+    entries/s of a full sweep over all training entries."""
+    b = max((t2 - t1) / max(m2 - m1, 1), 1e-12)
+    a = max(t1 - b * m1, 0.0)
+    t_full = a + b * prob.nnz
+    return prob.nnz / t_full, t_full
+
+
+def oracle_sample_text(m1, t1, m2, t2, t_full):
+    return (f"oracle ALS sweeps at the full n=65536 L=12 r=8 shape over 1% ({m1} entries, {t1:.1f} s) and "
+            f"2% ({m2} entries, {t2:.1f} s) of the training entries; t = a + b*entries fitted to the two "
+            f"and extrapolated to all 3774874 entries ({t_full:.0f} s per sweep)")
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    oracle.build()
+    prob = synth.config(3)
+    X0 = synth.random_factors(prob.n, prob.L, prob.r, prob.seed + synth.SEED_PLANT, sigma=0.3)
+    for _ in range(args.warmup):
+        time_oracle_sweep(prob, X0, 100)
+    times = []
+    m1 = 0
+    for _ in range(args.steps):
+        m1, dt = time_oracle_sweep(prob, X0, 100)
+        times.append(dt)
+    t1 = statistics.mean(times)
+    m2, t2 = time_oracle_sweep(prob, X0, 50)
+    value, t_full = oracle_full_rate(prob, m1, t1, m2, t2)
+    ms = 1e3 * t1
+    sample = ("each step: " + oracle_sample_text(m1, t1, m2, t2, t_full)
+              + "; ms_per_step is the 1% sweep")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "host, serial"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ our arm
+
+def run_bfc(args, rank, world, local_rank):
+    import torch
+
+    import paper_2510_17734_gb300 as bfc
+    import synth
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    bfc.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    prob = synth.config(3)
+    prec = bfc.PREC_C64 if args.prec == "c64" else bfc.PREC_FP64
+
+    c = lowrank_start(prob, bfc, prec)
+    stream = torch.cuda.Stream(device=dev)
+    bfc.bfc_set_stream(c.ctx, stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        c.sweep()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    c.profile(True)
+    stats = []
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            stats.append(c.sweep())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    prof = c.profile_read()
+    c.profile(False)
+    ms_step = ms_total / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * prob.nnz / (ms_step * 1e-3)
+
+    # end to end through the public API with host buffers (pinned)
+    P = c.P
+    host_in = torch.empty(2 * P, dtype=torch.float64, pin_memory=True)
+    host_out = torch.empty(2 * P, dtype=torch.float64, pin_memory=True)
+    host_in.copy_(torch.from_numpy(c.get_factors().view(np.float64)))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        bfc.bfc_set_factors(c.ctx, host_in)
+        bfc.bfc_als_sweep(c.ctx)
+        bfc.bfc_get_factors(c.ctx, host_out)
+    torch.cuda.synchronize()
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * prob.nnz / (e2e_ms * 1e-3)
+
+    # roofline of the dominant kernel (per-slice normal equations + solve)
+    launches = sum(v[0] for v in prof.values())
+    mid_n, mid_ms = prof.get("mid_gram_solve", (0, 0.0))
+    mid_avg_ms = mid_ms / max(mid_n, 1)
+    flops_per_launch = prob.nnz * als_flops_per_entry(prob.r)
+    clocks = clk.summary()
+    sm_max = load_peaks().get("sm_max_mhz", 2070.0)
+    peak_tflops = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops_per_launch / (mid_avg_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "k_mid (per-slice Gram + FP64 solve + left update)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64+f64" if prec == bfc.PREC_C64 else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.prec,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "working set > L2 (no flush)", "nnz_train": prob.nnz},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * P,
+                    "d2h_bytes_per_step": 16 * P + 64, "ms_per_step": e2e_ms},
+            "gpu_launches": launches,
+            "kernels_ms": {k: round(v[1] / max(args.steps, 1), 4) for k, v in prof.items()},
+            "roofline": roofline,
+            "clocks": clocks,
+            "sweep_stats": {"train_rel_err": stats[-1]["train_rel_err"],
+                            "test_rel_err": stats[-1]["test_rel_err"]}}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        X0 = c.get_factors()
+        m1, t1 = time_oracle_sweep(prob, X0, 100)
+        m2, t2 = time_oracle_sweep(prob, X0, 50)
+        v, t_full = oracle_full_rate(prob, m1, t1, m2, t2)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": oracle_sample_text(m1, t1, m2, t2, t_full)}
+    c.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="bfc", choices=["bfc", "reference"])
+    ap.add_argument("--prec", default="c64", choices=["c64", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        return run_bfc(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

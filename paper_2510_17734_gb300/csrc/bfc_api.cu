@@ -145,8 +145,14 @@ static bfc_status refresh_copies(Ctx* c)
 static bfc_status factor_sumsq(Ctx* c, int slot)
 {
     const int nb = (int)std::min<int64_t>(1216, (c->Pn + 255) / 256);
-    launch_sumsq(c->z1d, c->Pn, c->d_red, nb, c->stream);  // factors are contiguous (one allocation)
-    launch_reduce_single(c->d_red, nb, c->d_scalars + slot, c->stream);
+    {
+        ProfScope ps(c, "sumsq");
+        launch_sumsq(c->z1d, c->Pn, c->d_red, nb, c->stream);  // factors are contiguous (one allocation)
+    }
+    {
+        ProfScope ps(c, "reduce");
+        launch_reduce_single(c->d_red, nb, c->d_scalars + slot, c->stream);
+    }
     BFC_LAUNCH_CHECK(c, "sumsq");
     return BFC_OK;
 }
@@ -351,7 +357,10 @@ static bfc_status test_error(Ctx* c, int slot)
     const Ops* ops = get_ops(c->fp32, c->r);
     const int nb = (int)std::min<int64_t>(1216, (c->NT + 255) / 256);
     BFC_TRY(ops->eval(c, c->d_it, c->d_jt, c->NT, nullptr, c->d_tt, c->d_red, nb));
-    launch_reduce_pairs(c->d_red, nb, c->d_scalars + slot, c->stream);
+    {
+        ProfScope ps(c, "reduce");
+        launch_reduce_pairs(c->d_red, nb, c->d_scalars + slot, c->stream);
+    }
     BFC_LAUNCH_CHECK(c, "reduce");
     return BFC_OK;
 }
