@@ -204,6 +204,37 @@ bfc_status bfc_profile_enable(bfc_ctx* ctx, int32_t enable);
 bfc_status bfc_profile_read(bfc_ctx* ctx, bfc_kernel_profile* out, int32_t cap,
                             int32_t* count);
 
+/* Allocation-free residual sums.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- code embedded in a
+ * host application whose allocator or memory pool owns all device memory and
+ * forbids other allocations, and latency-sensitive callers that cannot
+ * accept an allocation (which may synchronize the device or fail) at call
+ * time.  It allocates nothing: no context, no cudaMalloc or cudaFree, no
+ * allocating library routine.
+ *
+ * Computes, for the butterfly with packed complex128 factors `factors` (the
+ * layout above, sizes n = b 2^L and rank r in [1, 10]), over m entries:
+ *     sums[0] = sum_e |t_e - x_{i_e j_e}|^2,   sums[1] = sum_e |t_e|^2
+ * (the two sums of Eq. (BF_convergence)), with FP64 entry evaluation.  All
+ * of factors, i, j, t (m interleaved complex128) and sums (2 doubles) are
+ * DEVICE pointers owned by the caller.  The work is enqueued on `stream` (a
+ * cudaStream_t, NULL = default stream) and the call returns without waiting;
+ * sums is valid once the stream reaches this point.
+ * Scratch: per-block partial sums live in one fixed file-scope device array
+ * of the library (256 KiB, held by every GPU that loads the library until the
+ * process exits), so m may be at most 4,194,304; larger m, bad sizes or NULL
+ * pointers return BFC_EINVAL (message in bfc_last_error(NULL)) without
+ * launching anything.  An index outside [0, n) makes both sums NaN.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  Every call shares the array and leaves its partials
+ * in it (the bad-index flag is cleared at the start of each call): calls that
+ * overlap on the GPU, on any streams, race and give wrong sums. */
+bfc_status bfc_residual_noalloc(int64_t n, int32_t L, int32_t b, int32_t r,
+                                const double* factors, int64_t m, const int32_t* i,
+                                const int32_t* j, const double* t, double* sums,
+                                void* stream);
+
 /* Message for the last failed call on ctx (or of the last failed
  * bfc_create when ctx is NULL).  Never NULL. */
 const char* bfc_last_error(const bfc_ctx* ctx);

@@ -25,7 +25,7 @@ __all__ = [
     "bfc_num_params", "bfc_create", "bfc_set_stream", "bfc_set_factors", "bfc_get_factors",
     "bfc_eval", "bfc_als_sweep", "bfc_grad", "bfc_lowrank_init", "bfc_complete",
     "bfc_profile_enable", "bfc_profile_read", "bfc_last_error", "bfc_destroy",
-    "bfc_decode", "bfc_get_order",
+    "bfc_decode", "bfc_get_order", "bfc_residual_noalloc",
 ]
 
 PREC_FP64 = 0
@@ -37,7 +37,7 @@ STATUS = {0: "BFC_OK", 1: "BFC_EINVAL", 2: "BFC_ENOMEM", 3: "BFC_ECUDA", 4: "BFC
 exported_symbols = (
     "bfc_num_params", "bfc_create", "bfc_set_stream", "bfc_set_factors", "bfc_get_factors",
     "bfc_eval", "bfc_als_sweep", "bfc_grad", "bfc_lowrank_init", "bfc_complete",
-    "bfc_decode", "bfc_get_order",
+    "bfc_decode", "bfc_get_order", "bfc_residual_noalloc",
     "bfc_profile_enable", "bfc_profile_read", "bfc_last_error", "bfc_destroy",
 )
 
@@ -118,6 +118,8 @@ def load():
         lib.bfc_decode.restype = i32
         lib.bfc_get_order.argtypes = [vp, i32, vp, vp]
         lib.bfc_get_order.restype = i32
+        lib.bfc_residual_noalloc.argtypes = [i64, i32, i32, i32, vp, i64, vp, vp, vp, vp, vp]
+        lib.bfc_residual_noalloc.restype = i32
         lib.bfc_profile_enable.argtypes = [vp, i32]
         lib.bfc_profile_enable.restype = i32
         lib.bfc_profile_read.argtypes = [vp, ctypes.POINTER(KernelProfile), i32, ctypes.POINTER(i32)]
@@ -229,6 +231,15 @@ def bfc_get_order(ctx, level: int, N: int, K: int):
     seg = np.zeros(K + 1, dtype=np.int32)
     _check(load().bfc_get_order(ctx, level, _ptr(perm), _ptr(seg)), ctx)
     return perm, seg
+
+
+def bfc_residual_noalloc(n: int, L: int, b: int, r: int, factors, i, j, t, sums, stream=None):
+    """Allocation-free residual sums on caller-owned device buffers (torch
+    CUDA tensors): sums[0] = sum |t - x|^2, sums[1] = sum |t|^2.  Enqueued on
+    `stream` (a raw cudaStream_t handle, None = default stream); no wait."""
+    m = int(i.shape[0])
+    _check(load().bfc_residual_noalloc(n, L, b, r, _ptr(factors), m, _ptr(i), _ptr(j), _ptr(t),
+                                       _ptr(sums), ctypes.c_void_p(stream or 0)), None)
 
 
 def bfc_profile_enable(ctx, enable: bool):
