@@ -93,6 +93,11 @@ typedef struct {
     int32_t values_on_device; /* 1: data pointers are device pointers        */
     int32_t refine_sweeps;  /* precision form: FP64 sweeps appended by
                                bfc_complete after the complex64 sweeps       */
+    double ridge_rel;       /* ridge floor: every system is solved with
+                               max(lambda, ridge_rel * trace(K) / dim).
+                               0 selects the default (2^-20, the complex64
+                               rounding level of the normal equations, in the
+                               precision form; none in FP64); < 0 disables  */
 } bfc_params;
 
 typedef struct {

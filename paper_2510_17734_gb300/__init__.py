@@ -54,7 +54,7 @@ class Params(ctypes.Structure):
                 ("max_sweeps", ctypes.c_int32), ("tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("init_kind", ctypes.c_int32), ("lr_rank", ctypes.c_int32),
                 ("lr_sweeps", ctypes.c_int32), ("values_on_device", ctypes.c_int32),
-                ("refine_sweeps", ctypes.c_int32)]
+                ("refine_sweeps", ctypes.c_int32), ("ridge_rel", ctypes.c_double)]
 
 
 class SweepStats(ctypes.Structure):
@@ -270,11 +270,11 @@ class Completion:
 
     def __init__(self, n, L, b, r, lam, i, j, t, it=None, jt=None, tt=None, prec=PREC_FP64,
                  max_sweeps=20, tol=1e-3, seed=0, init_kind=0, lr_rank=0, lr_sweeps=10,
-                 refine_sweeps=0):
+                 refine_sweeps=0, ridge_rel=0.0):
         self.n, self.L, self.b, self.r = int(n), int(L), int(b), int(r)
         self.params = Params(n=n, L=L, b=b, r=r, lam=lam, prec=prec, max_sweeps=max_sweeps, tol=tol,
                              seed=seed, init_kind=init_kind, lr_rank=lr_rank, lr_sweeps=lr_sweeps,
-                             values_on_device=0, refine_sweeps=refine_sweeps)
+                             values_on_device=0, refine_sweeps=refine_sweeps, ridge_rel=ridge_rel)
         self.P = bfc_num_params(n, L, b, r)
         self._nnz = len(i)
         self.ctx = bfc_create(self.params, i, j, t, it, jt, tt)

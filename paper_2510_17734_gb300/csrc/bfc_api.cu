@@ -288,6 +288,9 @@ static bfc_status build(Ctx* c, const Inputs& in)
         c->zLt = c->zLd;
     }
     const Ops* ops = get_ops(c->fp32, r);
+    BFC_TRY(dalloc(c, &c->rec, ops->record_bytes(n, S), "normal-equation records"));
+    const size_t fbb = ops->fallback_bytes(S);
+    if (fbb > 0 && L > 0) BFC_TRY(dalloc(c, (void**)&c->fb, fbb, "FP64 fallback"));
     BFC_TRY(ops->configure(c));
     return sync(c);
 }
@@ -300,6 +303,7 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
     if (!valid_sizes(p.n, p.L, p.b, p.r))
         return fail(nullptr, BFC_EINVAL, "invalid sizes: need n = b * 2^L, 0 <= L <= 24, 1 <= r <= 10");
     if (!(p.lambda >= 0.0) || !isfinite(p.lambda)) return fail(nullptr, BFC_EINVAL, "lambda must be finite and >= 0");
+    if (!isfinite(p.ridge_rel)) return fail(nullptr, BFC_EINVAL, "ridge_rel must be finite");
     if (p.prec != BFC_PREC_FP64 && p.prec != BFC_PREC_C64_FP64SOLVE)
         return fail(nullptr, BFC_EINVAL, "unknown precision");
     if (in.nnz <= 0 || in.nnz >= ((int64_t)1 << 31) - 1) return fail(nullptr, BFC_EINVAL, "nnz must be in [1, 2^31-2]");
@@ -318,6 +322,7 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
     c->Pn = bfc_num_params(p.n, p.L, p.b, p.r);
     c->fp32 = p.prec == BFC_PREC_C64_FP64SOLVE;
     c->vsz = c->fp32 ? 8 : 16;
+    c->ridge = p.ridge_rel > 0.0 ? p.ridge_rel : (p.ridge_rel == 0.0 && c->fp32 ? 9.5367431640625e-07 : 0.0);
     bfc_status st = build(c, in);
     if (st != BFC_OK) {
         g_create_err = c->err;

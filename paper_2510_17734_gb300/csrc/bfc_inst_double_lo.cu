@@ -6,7 +6,8 @@ namespace bfc {
 
 template <typename T, int R> static Ops make_ops()
 {
-    return Ops{&Path<T, R>::configure, &Path<T, R>::sweep, &Path<T, R>::grad, &Path<T, R>::eval};
+    return Ops{&Path<T, R>::configure, &Path<T, R>::sweep, &Path<T, R>::grad, &Path<T, R>::eval,
+               &Path<T, R>::record_bytes, &Path<T, R>::fallback_bytes};
 }
 
 const Ops* ops_double_lo(int r)

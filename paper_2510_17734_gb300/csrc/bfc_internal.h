@@ -34,6 +34,7 @@ struct Ctx {
     int64_t n = 0, N = 0, NT = 0, S = 0, Pn = 0;  // Pn: complex parameter count
     int L = 0, b = 0, r = 0;
     bool fp32 = false;              // compute type float (precision form) or double
+    double ridge = 0.0;             // effective ridge floor factor (ridge_rel resolved)
     size_t vsz = 16;                // bytes of one complex compute value
     cudaStream_t stream = nullptr, own_stream = nullptr;
     std::string err;
@@ -56,6 +57,8 @@ struct Ctx {
     void* W = nullptr;
     void* H[2] = {nullptr, nullptr};
     void* Rres[2] = {nullptr, nullptr};  // residual carried along the orders (gradient)
+    void* rec = nullptr;              // per-block normal-equation records [K packed | y]
+    double2* fb = nullptr;            // FP64 fallback factors (precision form)
 
     // factors: FP64 master and compute-type copies (alias when double)
     double2 *z1d = nullptr, *Zd = nullptr, *zLd = nullptr;

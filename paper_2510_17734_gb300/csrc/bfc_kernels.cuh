@@ -65,6 +65,22 @@ __device__ __forceinline__ void kahan(float& s, float& c, float x)
     s = t;
 }
 
+// Four consecutive complex values from 16-byte-aligned shared memory.
+__device__ __forceinline__ void load4(float2 (&d)[4], const float2* p)
+{
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    const float4 b = *reinterpret_cast<const float4*>(p + 2);
+    d[0] = make_float2(a.x, a.y);
+    d[1] = make_float2(a.z, a.w);
+    d[2] = make_float2(b.x, b.y);
+    d[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void load4(double2 (&d)[4], const double2* p)
+{
+#pragma unroll
+    for (int u = 0; u < 4; ++u) d[u] = p[u];
+}
+
 // Slice id of the middle factor S^{m+1}: psi^{-1}(i_0..i_{L-m}, j_0..j_{m-1}).
 __device__ __forceinline__ int slice_of(int pi, int pj, int m, int L)
 {
@@ -72,7 +88,7 @@ __device__ __forceinline__ int slice_of(int pi, int pj, int m, int L)
 }
 
 // Packed lower-triangular index (p >= q).
-__device__ __forceinline__ int tri(int p, int q) { return (p * (p + 1) >> 1) + q; }
+__host__ __device__ __forceinline__ constexpr int tri(int p, int q) { return (p * (p + 1) >> 1) + q; }
 
 // ------------------------------------------------------------------------
 // Right environments, one level: w_{m-1} = Z^{m+1}(k) w_m for every entry of
@@ -123,93 +139,103 @@ __global__ void k_env_init(typename cvec<T>::type* __restrict__ WL,
 }
 
 // ------------------------------------------------------------------------
-// Serial Hermitian Cholesky solve of a small system (one thread), packed
-// lower storage K (D(D+1)/2 entries).  Returns false when a pivot <= tol.
-__device__ inline bool chol_solve_serial(double2* K, const double2* y, double2* s, int D,
-                                         double tol)
+// Normal equations of Alg. 1 (complex form): for a block (one fiber of S^1 or
+// S^{L+2}, or one slice of a middle factor) with design vectors a_e,
+//   K = sum conj(a_e) a_e^T + lambda I,   y = sum conj(a_e) t_e,   K s = y.
+// Every kernel that accumulates K and y writes them, packed lower-triangular
+// (element (p, q), p >= q, at tri(p, q)) followed by y, to a per-block
+// record; a solve kernel then factors and solves.
+//
+// FP64 on this GPU runs at 1/64 of the FP32 rate and a warp-wide FP64
+// instruction holds an SM sub-partition's FP64 pipe for tens of cycles
+// whatever the number of active lanes, so every FP64 stage below keeps all 32
+// lanes busy: small systems are solved one per thread, large ones with rows
+// spread over the lanes.
+
+template <typename E> __device__ __forceinline__ void csub_mul_conj(E& acc, E a, E b)
 {
-    for (int c = 0; c < D; ++c) {
+    // acc -= a * conj(b)
+    acc.x -= a.x * b.x + a.y * b.y;
+    acc.y -= a.y * b.x - a.x * b.y;
+}
+
+// Hermitian Cholesky + two triangular solves for one small system held by one
+// thread (R compile-time: the loops unroll and K, y stay in registers).
+// K: packed lower (R(R+1)/2), y: right-hand side, overwritten by the solution.
+template <int R>
+__device__ __forceinline__ bool thread_chol_solve(double2 (&K)[R * (R + 1) / 2], double2 (&y)[R], double tol)
+{
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
         double d = K[tri(c, c)].x;
-        for (int q = 0; q < c; ++q) {
-            double2 l = K[tri(c, q)];
-            d -= l.x * l.x + l.y * l.y;
-        }
+#pragma unroll
+        for (int q = 0; q < c; ++q) d -= K[tri(c, q)].x * K[tri(c, q)].x + K[tri(c, q)].y * K[tri(c, q)].y;
         if (!(d > tol)) return false;
-        double piv = sqrt(d), inv = 1.0 / piv;
-        K[tri(c, c)] = make_double2(piv, 0.0);
-        for (int row = c + 1; row < D; ++row) {
+        const double piv = sqrt(d), inv = 1.0 / piv;
+        K[tri(c, c)] = make_double2(piv, inv);  // .y keeps 1/piv for the solves
+#pragma unroll
+        for (int row = c + 1; row < R; ++row) {
             double2 acc = K[tri(row, c)];
-            for (int q = 0; q < c; ++q) {
-                double2 a = K[tri(row, q)], bq = K[tri(c, q)];
-                // acc -= a * conj(bq)
-                acc.x -= a.x * bq.x + a.y * bq.y;
-                acc.y -= a.y * bq.x - a.x * bq.y;
-            }
+#pragma unroll
+            for (int q = 0; q < c; ++q) csub_mul_conj(acc, K[tri(row, q)], K[tri(c, q)]);
             K[tri(row, c)] = make_double2(acc.x * inv, acc.y * inv);
         }
     }
-    for (int row = 0; row < D; ++row) {
+#pragma unroll
+    for (int row = 0; row < R; ++row) {
         double2 acc = y[row];
+#pragma unroll
         for (int q = 0; q < row; ++q) {
-            double2 l = K[tri(row, q)], z = s[q];
+            const double2 l = K[tri(row, q)], z = y[q];
             acc.x -= l.x * z.x - l.y * z.y;
             acc.y -= l.x * z.y + l.y * z.x;
         }
-        double inv = 1.0 / K[tri(row, row)].x;
-        s[row] = make_double2(acc.x * inv, acc.y * inv);
+        const double inv = K[tri(row, row)].y;
+        y[row] = make_double2(acc.x * inv, acc.y * inv);
     }
-    for (int row = D - 1; row >= 0; --row) {
-        double2 acc = s[row];
-        for (int q = row + 1; q < D; ++q) {
-            double2 l = K[tri(q, row)], z = s[q];
-            // acc -= conj(l) * z
+#pragma unroll
+    for (int row = R - 1; row >= 0; --row) {
+        double2 acc = y[row];
+#pragma unroll
+        for (int q = row + 1; q < R; ++q) {
+            const double2 l = K[tri(q, row)], z = y[q];
             acc.x -= l.x * z.x + l.y * z.y;
             acc.y -= l.x * z.y - l.y * z.x;
         }
-        double inv = 1.0 / K[tri(row, row)].x;
-        s[row] = make_double2(acc.x * inv, acc.y * inv);
+        const double inv = K[tri(row, row)].y;
+        y[row] = make_double2(acc.x * inv, acc.y * inv);
     }
     return true;
 }
 
 // ------------------------------------------------------------------------
-// Outer fibers (S^1 rows when COLS is false, S^{L+2} columns when true):
-// one warp per fiber f.  Design vector a_e = A[p] (w_0 for rows, h_{L+1} for
-// columns), K = sum conj(a) a^T + lambda I (r x r), y = sum conj(a) t,
-// solved in FP64 (Alg. 1, first and last branches, complex form).
-// Rows then write h_1 = z1(i, :) for every entry into order 1; columns
-// evaluate x = h_{L+1}^T zL(j) and accumulate the training residual.
-template <typename T, int R, bool COLS>
+// Outer fibers, stage 1: one warp per fiber accumulates K and y (r x r) over
+// the fiber's entries.  A: design vectors in the level order (w_0 for the S^1
+// rows, h_{L+1} for the S^{L+2} columns).  Lanes own the R(R+1)/2 + R items;
+// in float the per-chunk partials are folded into Kahan-compensated sums.
+// Output record per fiber: [K packed (R(R+1)/2) | y (R)] in FP64.
+template <typename T, int R>
 __global__ void __launch_bounds__(128)
-k_outer(const typename cvec<T>::type* __restrict__ A, const typename cvec<T>::type* __restrict__ tv,
-        const int32_t* __restrict__ seg, int nfib, double lambda, double2* __restrict__ zd,
-        typename cvec<T>::type* __restrict__ zt, const int32_t* __restrict__ nxt,
-        typename cvec<T>::type* __restrict__ Hn, double* __restrict__ err_part,
-        unsigned long long* __restrict__ nsing)
+k_outer_gram(const typename cvec<T>::type* __restrict__ A, const typename cvec<T>::type* __restrict__ tv,
+             const int32_t* __restrict__ seg, int nfib, double2* __restrict__ rec)
 {
     typedef typename cvec<T>::type V;
     constexpr bool COMP = sizeof(T) == 4;
     constexpr int NP = R * (R + 1) / 2;
     constexpr int NI = NP + R;
     constexpr int IPL = (NI + 31) / 32;
-    constexpr int WPB = 4;  // warps (fibers) per 128-thread block
+    constexpr int WPB = 4;
     __shared__ V a_s[WPB][32 * R];
     __shared__ V t_s[WPB][32];
-    __shared__ double2 K_s[WPB][NP];
-    __shared__ double2 y_s[WPB][R];
-    __shared__ double2 x_s[WPB][R];
-    __shared__ int ok_s[WPB];
-
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int f = blockIdx.x * WPB + wib;
-    if (f >= nfib) return;                       // whole warp leaves; no block barriers below
+    if (f >= nfib) return;  // whole warp leaves; only warp-level barriers below
     const int s0 = seg[f], s1 = seg[f + 1];
 
-    // item -> (p, q) (pair, p >= q) or rhs index
     int ip[IPL], iq[IPL];
 #pragma unroll
     for (int u = 0; u < IPL; ++u) {
-        int it = lane + 32 * u;
+        const int it = lane + 32 * u;
         ip[u] = -1;
         iq[u] = -1;
         if (it < NP) {
@@ -219,7 +245,7 @@ k_outer(const typename cvec<T>::type* __restrict__ A, const typename cvec<T>::ty
             iq[u] = it - p * (p + 1) / 2;
         } else if (it < NI) {
             ip[u] = it - NP;
-            iq[u] = -2;  // rhs
+            iq[u] = -2;  // right-hand side item
         }
     }
     V acc[IPL], sum[IPL], cmp[IPL];
@@ -254,37 +280,72 @@ k_outer(const typename cvec<T>::type* __restrict__ A, const typename cvec<T>::ty
             }
         }
     }
-    // assemble the system in FP64
 #pragma unroll
     for (int u = 0; u < IPL; ++u) {
-        double2 v = COMP ? make_double2((double)sum[u].x - (double)cmp[u].x,
-                                        (double)sum[u].y - (double)cmp[u].y)
-                         : to_d2(acc[u]);
-        if (iq[u] >= 0) K_s[wib][tri(ip[u], iq[u])] = v;
-        else if (iq[u] == -2) y_s[wib][ip[u]] = v;
-    }
-    __syncwarp();
-    if (lane == 0) {
-        double trace = 0.0;
-        for (int p = 0; p < R; ++p) {
-            K_s[wib][tri(p, p)].x += lambda;
-            trace += K_s[wib][tri(p, p)].x;
+        const int it = lane + 32 * u;
+        if (it < NI) {
+            const double2 v = COMP ? make_double2((double)sum[u].x - (double)cmp[u].x,
+                                                  (double)sum[u].y - (double)cmp[u].y)
+                                   : to_d2(acc[u]);
+            rec[(size_t)f * NI + it] = v;
         }
-        const double tol = lambda > 0.0 ? 0.0 : 1e-14 * trace;
-        ok_s[wib] = chol_solve_serial(K_s[wib], y_s[wib], x_s[wib], R, tol) ? 1 : 0;
-        if (!ok_s[wib]) atomicAdd(nsing, 1ull);
     }
-    __syncwarp();
-    const bool ok = ok_s[wib] != 0;
-    if (ok && lane < R) {
-        zd[(size_t)f * R + lane] = x_s[wib][lane];
-        zt[(size_t)f * R + lane] = from_d2<V>(x_s[wib][lane]);
+}
+
+// Outer fibers, stage 2: one thread per fiber solves K + lambda I in FP64
+// (32 independent fibers per warp keep every lane of the FP64 pipe busy).
+// A system whose pivot falls to <= tol keeps its old fiber and is counted.
+template <typename T, int R>
+__global__ void __launch_bounds__(64)
+k_outer_solve(const double2* __restrict__ rec, int nfib, double lambda, double ridge, double2* __restrict__ zd,
+              typename cvec<T>::type* __restrict__ zt, unsigned long long* __restrict__ nsing)
+{
+    typedef typename cvec<T>::type V;
+    constexpr int NP = R * (R + 1) / 2;
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfib) return;
+    double2 K[NP], y[R];
+    const double2* src = rec + (size_t)f * (NP + R);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) K[q] = src[q];
+#pragma unroll
+    for (int q = 0; q < R; ++q) y[q] = src[NP + q];
+    double tr0 = 0.0;
+#pragma unroll
+    for (int p = 0; p < R; ++p) tr0 += K[tri(p, p)].x;
+    const double lam = fmax(lambda, ridge * tr0 / R);
+#pragma unroll
+    for (int p = 0; p < R; ++p) K[tri(p, p)].x += lam;
+    const double tol = lam > 0.0 ? 0.0 : 1e-14 * (tr0 + R * lam);
+    if (thread_chol_solve<R>(K, y, tol)) {
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+            zd[(size_t)f * R + c] = y[c];
+            zt[(size_t)f * R + c] = from_d2<V>(y[c]);
+        }
+    } else {
+        atomicAdd(nsing, 1ull);
     }
-    __syncwarp();
+}
+
+// Outer fibers, stage 3 (one warp per fiber).  Rows (S^1): h_1 = z1(i, :) for
+// every entry, written into order 1.  Columns (S^{L+2}): x = h_{L+1}^T zL(j),
+// per-fiber sums of |t - x|^2 and |t|^2 for the training error.
+template <typename T, int R, bool COLS>
+__global__ void __launch_bounds__(128)
+k_outer_post(const typename cvec<T>::type* __restrict__ A, const typename cvec<T>::type* __restrict__ tv,
+             const int32_t* __restrict__ seg, int nfib, const typename cvec<T>::type* __restrict__ zt,
+             const int32_t* __restrict__ nxt, typename cvec<T>::type* __restrict__ Hn,
+             double* __restrict__ err_part)
+{
+    typedef typename cvec<T>::type V;
+    const int lane = threadIdx.x & 31;
+    const int f = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (f >= nfib) return;
+    const int s0 = seg[f], s1 = seg[f + 1];
     V zf[R];
 #pragma unroll
-    for (int c = 0; c < R; ++c) zf[c] = ok ? from_d2<V>(x_s[wib][c]) : zt[(size_t)f * R + c];
-
+    for (int c = 0; c < R; ++c) zf[c] = zt[(size_t)f * R + c];
     if (!COLS) {
         for (int p = s0 + lane; p < s1; p += 32) {
             const size_t o = (size_t)nxt[p] * R;
@@ -297,8 +358,8 @@ k_outer(const typename cvec<T>::type* __restrict__ A, const typename cvec<T>::ty
             V x = czero<V>();
 #pragma unroll
             for (int c = 0; c < R; ++c) cmac(x, A[(size_t)p * R + c], zf[c]);
-            V t = tv[p];
-            double dx = (double)t.x - (double)x.x, dy = (double)t.y - (double)x.y;
+            const V t = tv[p];
+            const double dx = (double)t.x - (double)x.x, dy = (double)t.y - (double)x.y;
             num += dx * dx + dy * dy;
             den += (double)t.x * (double)t.x + (double)t.y * (double)t.y;
         }
@@ -315,55 +376,51 @@ k_outer(const typename cvec<T>::type* __restrict__ A, const typename cvec<T>::ty
 }
 
 // ------------------------------------------------------------------------
-// Middle level m: one CTA per slice k of S^{m+1}.
-//   Gram/RHS: a_e = h_m(e) (x) w_m(e) (a[p r + c] = h_p w_c), K = sum conj(a) a^T,
-//   y = sum conj(a) t over the slice's entries (Alg. 1 middle branch, complex
-//   form).  Threads own 4x4 complex tiles of the lower triangle of K, entries
-//   are split over G thread groups and staged in shared memory in chunks of
-//   CE.  In float the chunk partials are folded into Kahan-compensated sums.
-//   Solve: K + lambda I in FP64, Cholesky (CTA-parallel right-looking on
-//   packed storage) + triangular solves; the slice is written row-major.
-//   Left update: h_{m+1}(e) = h_m(e)^T Z^{m+1}(k) scattered into order m+1.
-template <typename T, int R> struct MidCfg {
+// Middle level m, stage 1 (Gram): one CTA per slice k of S^{m+1}.
+//   a_e = h_m(e) (x) w_m(e), a[p r + c] = h_p w_c, K = sum conj(a) a^T,
+//   y = sum conj(a) t over the slice's entries (Alg. 1 middle branch).
+// Threads own 4x4 complex tiles of the lower triangle of K; entries are
+// staged in shared memory in chunks of CE and split over G thread groups.  In
+// float every chunk partial (registers) is folded into a Kahan-compensated
+// running sum (sum in registers, compensation in shared memory, so several
+// CTAs fit on one SM).  Output record per slice: [K packed | y] in the compute
+// type (the compensated sums rounded once).
+template <typename T, int R> struct GramCfg {
     static constexpr int D = R * R;
     static constexpr int DP = (D + 3) / 4 * 4;
     static constexpr int NB = DP / 4;
     static constexpr int NT = NB * (NB + 1) / 2;
-    static constexpr int CE = (DP <= 36) ? 64 : 32;
-    static constexpr int GT = (288 / NT) < 1 ? 1 : (288 / NT);
+    static constexpr int CE = (DP <= 64) ? 64 : 32;
+    static constexpr int GT = (160 / NT) < 1 ? 1 : (160 / NT);
     static constexpr int G = GT > CE ? CE : GT;
     static constexpr int NTH = ((NT * G + 31) / 32) * 32;
     static constexpr bool COMP = sizeof(T) == 4;
-    static constexpr int CSTRIDE = 40;  // floats of compensation per worker thread
-    static constexpr size_t KBYTES = (size_t)D * (D + 1) / 2 * sizeof(double2);
-    static constexpr size_t CBYTES = COMP ? (size_t)NTH * CSTRIDE * sizeof(float) : 0;
-    static constexpr size_t UBYTES = KBYTES > CBYTES ? KBYTES : CBYTES;
+    static constexpr int NPK = D * (D + 1) / 2;
+    static constexpr int CSTRIDE = 40;  // compensation floats per worker thread
     static constexpr size_t VS = sizeof(typename cvec<T>::type);
-    static constexpr size_t SMEM = (size_t)CE * DP * VS + (size_t)CE * VS + ((UBYTES + 15) / 16) * 16 +
-                                   2 * (size_t)DP * sizeof(double2) + (size_t)DP * VS + 16;
+    static constexpr size_t CBYTES = COMP ? (size_t)NTH * CSTRIDE * sizeof(float) : 0;
+    static constexpr size_t KBYTES = G > 1 ? (size_t)(NPK + D) * sizeof(double2) : 0;
+    static constexpr size_t UBYTES = ((CBYTES > KBYTES ? CBYTES : KBYTES) + 15) / 16 * 16;
+    static constexpr size_t SMEM = 2 * (size_t)CE * R * VS + (size_t)CE * DP * VS + (size_t)CE * VS + UBYTES + 16;
 };
 
 template <typename T, int R>
-__global__ void __launch_bounds__(MidCfg<T, R>::NTH)
-k_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>::type* __restrict__ Wm,
-      const typename cvec<T>::type* __restrict__ tv, const int32_t* __restrict__ seg,
-      const int32_t* __restrict__ nxt, typename cvec<T>::type* __restrict__ Hn,
-      double2* __restrict__ Zd, typename cvec<T>::type* __restrict__ Zt, double lambda,
-      unsigned long long* __restrict__ nsing, int S)
+__global__ void __launch_bounds__(GramCfg<T, R>::NTH)
+k_mid_gram(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>::type* __restrict__ Wm,
+           const typename cvec<T>::type* __restrict__ tv, const int32_t* __restrict__ seg,
+           typename cvec<T>::type* __restrict__ rec, int S)
 {
     typedef typename cvec<T>::type V;
-    typedef MidCfg<T, R> C;
-    constexpr int D = C::D, DP = C::DP;
+    typedef GramCfg<T, R> C;
+    constexpr int D = C::D, DP = C::DP, NPK = C::NPK;
     extern __shared__ __align__(16) unsigned char smem[];
-    V* a_s = (V*)smem;
+    V* h_s = (V*)smem;
+    V* w_s = h_s + C::CE * R;
+    V* a_s = w_s + C::CE * R;
     V* t_s = a_s + C::CE * DP;
     unsigned char* U = (unsigned char*)(t_s + C::CE);
-    double2* K_s = (double2*)U;
     float* c_s = (float*)U;
-    double2* y_s = (double2*)(U + ((C::UBYTES + 15) / 16) * 16);
-    double2* x_s = y_s + DP;
-    V* zt_s = (V*)(x_s + DP);
-    int* flag_s = (int*)(zt_s + DP);
+    double2* Kacc = (double2*)U;
 
     const int tid = threadIdx.x;
     const int nth = blockDim.x;
@@ -391,23 +448,28 @@ k_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>::type
         for (int base = s0; base < s1; base += C::CE) {
             const int cnt = min(C::CE, s1 - base);
             __syncthreads();
+            for (int q = tid; q < cnt * R; q += nth) {
+                h_s[q] = H[(size_t)base * R + q];
+                w_s[q] = Wm[(size_t)base * R + q];
+            }
+            for (int e = tid; e < cnt; e += nth) t_s[e] = tv[base + e];
+            __syncthreads();
             for (int idx = tid; idx < cnt * DP; idx += nth) {
                 const int e = idx / DP, q = idx - e * DP;
                 V a = czero<V>();
                 if (q < D) {
                     const int pa = q / R, pc = q - pa * R;
-                    a = cmul(H[(size_t)(base + e) * R + pa], Wm[(size_t)(base + e) * R + pc]);
+                    a = cmul(h_s[e * R + pa], w_s[e * R + pc]);
                 }
-                a_s[e * DP + q] = a;
+                a_s[idx] = a;
             }
-            for (int e = tid; e < cnt; e += nth) t_s[e] = tv[base + e];
             __syncthreads();
             if (worker) {
                 for (int e = grp; e < cnt; e += C::G) {
                     const V* ae = a_s + e * DP;
                     V ap[4], aq[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) { ap[u] = ae[I * 4 + u]; aq[u] = ae[J * 4 + u]; }
+                    load4(ap, ae + I * 4);
+                    load4(aq, ae + J * 4);
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -424,24 +486,20 @@ k_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>::type
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
                             float sx = (float)sum[u][v].x, sy = (float)sum[u][v].y;
-                            float cx = c_s[(2 * (u * 4 + v)) * C::NTH + tid];
-                            float cy = c_s[(2 * (u * 4 + v) + 1) * C::NTH + tid];
+                            float& cx = c_s[(2 * (u * 4 + v)) * C::NTH + tid];
+                            float& cy = c_s[(2 * (u * 4 + v) + 1) * C::NTH + tid];
                             kahan(sx, cx, (float)acc[u][v].x);
                             kahan(sy, cy, (float)acc[u][v].y);
                             sum[u][v].x = sx; sum[u][v].y = sy;
-                            c_s[(2 * (u * 4 + v)) * C::NTH + tid] = cx;
-                            c_s[(2 * (u * 4 + v) + 1) * C::NTH + tid] = cy;
                             acc[u][v] = czero<V>();
                         }
                         if (diag) {
                             float sx = (float)ysum[u].x, sy = (float)ysum[u].y;
-                            float cx = c_s[(32 + 2 * u) * C::NTH + tid];
-                            float cy = c_s[(32 + 2 * u + 1) * C::NTH + tid];
+                            float& cx = c_s[(32 + 2 * u) * C::NTH + tid];
+                            float& cy = c_s[(32 + 2 * u + 1) * C::NTH + tid];
                             kahan(sx, cx, (float)yacc[u].x);
                             kahan(sy, cy, (float)yacc[u].y);
                             ysum[u].x = sx; ysum[u].y = sy;
-                            c_s[(32 + 2 * u) * C::NTH + tid] = cx;
-                            c_s[(32 + 2 * u + 1) * C::NTH + tid] = cy;
                             yacc[u] = czero<V>();
                         }
                     }
@@ -449,30 +507,23 @@ k_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>::type
             }
         }
         __syncthreads();
-        // final per-thread values (compensated in float), held in acc / yacc
-        if (worker) {
+        if (C::COMP && worker) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
-                    if (C::COMP) {
-                        acc[u][v].x = sum[u][v].x - c_s[(2 * (u * 4 + v)) * C::NTH + tid];
-                        acc[u][v].y = sum[u][v].y - c_s[(2 * (u * 4 + v) + 1) * C::NTH + tid];
-                    }
+                    acc[u][v].x = sum[u][v].x - c_s[(2 * (u * 4 + v)) * C::NTH + tid];
+                    acc[u][v].y = sum[u][v].y - c_s[(2 * (u * 4 + v) + 1) * C::NTH + tid];
                 }
-                if (C::COMP && diag) {
+                if (diag) {
                     yacc[u].x = ysum[u].x - c_s[(32 + 2 * u) * C::NTH + tid];
                     yacc[u].y = ysum[u].y - c_s[(32 + 2 * u + 1) * C::NTH + tid];
                 }
             }
         }
-        __syncthreads();
-        for (int q = tid; q < D * (D + 1) / 2; q += nth) K_s[q] = make_double2(0.0, 0.0);
-        for (int q = tid; q < DP; q += nth) y_s[q] = make_double2(0.0, 0.0);
-        __syncthreads();
-        // deterministic reduction over the entry groups
-        for (int g = 0; g < C::G; ++g) {
-            if (worker && grp == g) {
+        V* out = rec + (size_t)k * (NPK + D);
+        if (C::G == 1) {
+            if (worker) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int p = I * 4 + u;
@@ -480,125 +531,359 @@ k_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>::type
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
                             const int q = J * 4 + v;
-                            if (q <= p) {
-                                double2 cur = K_s[tri(p, q)];
-                                cur.x += (double)acc[u][v].x;
-                                cur.y += (double)acc[u][v].y;
-                                K_s[tri(p, q)] = cur;
-                            }
+                            if (q <= p) out[tri(p, q)] = acc[u][v];
                         }
-                        if (diag) {
-                            y_s[p].x += (double)yacc[u].x;
-                            y_s[p].y += (double)yacc[u].y;
-                        }
+                        if (diag) out[NPK + p] = yacc[u];
                     }
                 }
             }
+        } else {
+            __syncthreads();  // compensation reads done before Kacc overwrites them
+            for (int q = tid; q < NPK + D; q += nth) Kacc[q] = make_double2(0.0, 0.0);
             __syncthreads();
-        }
-        // regularize, pivot threshold
-        if (tid == 0) {
-            double trace = 0.0;
-            for (int p = 0; p < D; ++p) {
-                K_s[tri(p, p)].x += lambda;
-                trace += K_s[tri(p, p)].x;
-            }
-            flag_s[0] = 1;
-            reinterpret_cast<double*>(flag_s + 2)[0] = lambda > 0.0 ? 0.0 : 1e-14 * trace;
-        }
-        __syncthreads();
-        const double tol = reinterpret_cast<double*>(flag_s + 2)[0];
-        // right-looking Cholesky K = L L^H on packed lower storage
-        for (int c = 0; c < D; ++c) {
-            if (tid == 0) {
-                const double d = K_s[tri(c, c)].x;
-                if (d > tol) {
-                    K_s[tri(c, c)] = make_double2(sqrt(d), 0.0);
-                } else {
-                    flag_s[0] = 0;
-                }
-            }
-            __syncthreads();
-            if (!flag_s[0]) break;
-            const double inv = 1.0 / K_s[tri(c, c)].x;
-            for (int row = c + 1 + tid; row < D; row += nth) {
-                double2 l = K_s[tri(row, c)];
-                K_s[tri(row, c)] = make_double2(l.x * inv, l.y * inv);
-            }
-            __syncthreads();
-            const int m = D - c - 1;
-            const int npairs = m * (m + 1) / 2;
-            for (int idx = tid; idx < npairs; idx += nth) {
-                int rr = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-                while ((rr + 1) * (rr + 2) / 2 <= idx) ++rr;
-                while (rr * (rr + 1) / 2 > idx) --rr;
-                const int qq = idx - rr * (rr + 1) / 2;
-                const int r_ = c + 1 + rr, q_ = c + 1 + qq;
-                const double2 a = K_s[tri(r_, c)], bq = K_s[tri(q_, c)];
-                double2 cur = K_s[tri(r_, q_)];
-                // cur -= a * conj(bq)
-                cur.x -= a.x * bq.x + a.y * bq.y;
-                cur.y -= a.y * bq.x - a.x * bq.y;
-                K_s[tri(r_, q_)] = cur;
-            }
-            __syncthreads();
-        }
-        const bool ok = flag_s[0] != 0;
-        if (ok && tid < 32) {
-            // forward L z = y (z kept in x_s), then backward L^H x = z
-            for (int row = 0; row < D; ++row) {
-                double px = 0.0, py = 0.0;
-                for (int q = tid; q < row; q += 32) {
-                    const double2 l = K_s[tri(row, q)], z = x_s[q];
-                    px += l.x * z.x - l.y * z.y;
-                    py += l.x * z.y + l.y * z.x;
-                }
+            for (int g = 0; g < C::G; ++g) {  // deterministic order over the groups
+                if (worker && grp == g) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    px += __shfl_xor_sync(0xffffffffu, px, o);
-                    py += __shfl_xor_sync(0xffffffffu, py, o);
-                }
-                if (tid == 0) {
-                    const double inv = 1.0 / K_s[tri(row, row)].x;
-                    x_s[row] = make_double2((y_s[row].x - px) * inv, (y_s[row].y - py) * inv);
-                }
-                __syncwarp();
-            }
-            for (int row = D - 1; row >= 0; --row) {
-                double px = 0.0, py = 0.0;
-                for (int q = row + 1 + tid; q < D; q += 32) {
-                    const double2 l = K_s[tri(q, row)], z = x_s[q];
-                    px += l.x * z.x + l.y * z.y;
-                    py += l.x * z.y - l.y * z.x;
-                }
+                    for (int u = 0; u < 4; ++u) {
+                        const int p = I * 4 + u;
+                        if (p < D) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    px += __shfl_xor_sync(0xffffffffu, px, o);
-                    py += __shfl_xor_sync(0xffffffffu, py, o);
+                            for (int v = 0; v < 4; ++v) {
+                                const int q = J * 4 + v;
+                                if (q <= p) {
+                                    Kacc[tri(p, q)].x += (double)acc[u][v].x;
+                                    Kacc[tri(p, q)].y += (double)acc[u][v].y;
+                                }
+                            }
+                            if (diag) {
+                                Kacc[NPK + p].x += (double)yacc[u].x;
+                                Kacc[NPK + p].y += (double)yacc[u].y;
+                            }
+                        }
+                    }
                 }
-                if (tid == 0) {
-                    const double inv = 1.0 / K_s[tri(row, row)].x;
-                    x_s[row] = make_double2((x_s[row].x - px) * inv, (x_s[row].y - py) * inv);
+                __syncthreads();
+            }
+            for (int q = tid; q < NPK + D; q += nth) out[q] = from_d2<V>(Kacc[q]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// Warp-level Hermitian Cholesky (K = L L^H) of a D x D packed lower matrix
+// in shared or global memory.  Right-looking; the trailing update of each
+// column is flattened over all (row, col) pairs so every lane has work.  The
+// diagonal of L is real, so its imaginary slot stores 1 / L_cc for the
+// triangular solves.  Returns false (warp-uniform) when a pivot is <= tol.
+template <typename E, typename S>
+__device__ bool warp_chol(E* Lm, int D, S tol, int lane)
+{
+    for (int c = 0; c < D; ++c) {
+        __syncwarp();
+        const S d = Lm[tri(c, c)].x;
+        if (!(d > tol)) return false;
+        const S piv = sqrt(d), inv = S(1) / piv;
+        __syncwarp();
+        if (lane == 0) {
+            E v;
+            v.x = piv;
+            v.y = inv;  // the factor's diagonal is real: its imaginary slot keeps 1 / L_cc
+            Lm[tri(c, c)] = v;
+        }
+        for (int row = c + 1 + lane; row < D; row += 32) {
+            E l = Lm[tri(row, c)];
+            l.x *= inv;
+            l.y *= inv;
+            Lm[tri(row, c)] = l;
+        }
+        __syncwarp();
+        const int m = D - c - 1;
+        const int npairs = m * (m + 1) / 2;
+        int rr = 0, qq = lane;
+        while (rr < m && qq > rr) { qq -= rr + 1; ++rr; }
+        for (int idx = lane; idx < npairs; idx += 32) {
+            const int r_ = c + 1 + rr, q_ = c + 1 + qq;
+            const E a = Lm[tri(r_, c)], bq = Lm[tri(q_, c)];
+            E cur = Lm[tri(r_, q_)];
+            csub_mul_conj(cur, a, bq);
+            Lm[tri(r_, q_)] = cur;
+            qq += 32;
+            while (rr < m && qq > rr) { qq -= rr + 1; ++rr; }
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+// Column-oriented triangular solves with the right-hand side spread over the
+// lanes: row p lives in slot p / 32 of lane p % 32.  L z = b, then L^H x = z.
+template <typename E, typename S, int NS>
+__device__ __forceinline__ void warp_chol_solve(const E* Lm, int D, E (&bv)[NS], int lane)
+{
+#pragma unroll
+    for (int slot = 0; slot < NS; ++slot) {
+        for (int owner = 0; owner < 32; ++owner) {
+            const int p = slot * 32 + owner;
+            if (p >= D) break;
+            E zp;
+            zp.x = __shfl_sync(0xffffffffu, bv[slot].x, owner);
+            zp.y = __shfl_sync(0xffffffffu, bv[slot].y, owner);
+            const S inv = Lm[tri(p, p)].y;
+            zp.x *= inv;
+            zp.y *= inv;
+            if (lane == owner) bv[slot] = zp;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int q = lane + 32 * s;
+                if (q > p && q < D) {
+                    const E l = Lm[tri(q, p)];
+                    bv[s].x -= l.x * zp.x - l.y * zp.y;
+                    bv[s].y -= l.x * zp.y + l.y * zp.x;
                 }
-                __syncwarp();
             }
         }
-        __syncthreads();
-        if (!ok && tid == 0) atomicAdd(nsing, 1ull);
-        for (int q = tid; q < D; q += nth) {
+    }
+#pragma unroll
+    for (int slot = NS - 1; slot >= 0; --slot) {
+        for (int owner = 31; owner >= 0; --owner) {
+            const int p = slot * 32 + owner;
+            if (p >= D) continue;
+            E xp;
+            xp.x = __shfl_sync(0xffffffffu, bv[slot].x, owner);
+            xp.y = __shfl_sync(0xffffffffu, bv[slot].y, owner);
+            const S inv = Lm[tri(p, p)].y;
+            xp.x *= inv;
+            xp.y *= inv;
+            if (lane == owner) bv[slot] = xp;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int q = lane + 32 * s;
+                if (q < p) {
+                    const E l = Lm[tri(p, q)];   // conj(l) * xp
+                    bv[s].x -= l.x * xp.x + l.y * xp.y;
+                    bv[s].y -= l.x * xp.y - l.y * xp.x;
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int R> struct SolveCfg {
+    static constexpr int D = R * R;
+    static constexpr int NPK = D * (D + 1) / 2;
+    static constexpr int NS = (D + 31) / 32;
+    static constexpr bool MIXED = sizeof(T) == 4;
+    // per warp: factor (compute type, padded to 16 bytes), FP64 solution
+    // vector, new slice (compute type)
+    static constexpr size_t LBYTES = ((size_t)NPK * sizeof(typename cvec<T>::type) + 15) / 16 * 16;
+    static constexpr size_t WBYTES = (LBYTES + (size_t)D * sizeof(double2) +
+                                      (size_t)D * sizeof(typename cvec<T>::type) + (size_t)D * sizeof(T) + 15) /
+                                     16 * 16;
+    static constexpr int WPB0 = (int)((96 * 1024) / WBYTES);
+    static constexpr int WPB = WPB0 < 1 ? 1 : (WPB0 > 4 ? 4 : WPB0);
+    static constexpr size_t SMEM = WBYTES * WPB;
+};
+
+// Middle level m, stage 2 (solve + left update): one warp per slice.
+// Precision form (float): complex64 Cholesky of the Jacobi-equilibrated
+// S (K + lambda I) S, complex64 solve, then up to three steps of FP64
+// iterative refinement (residual y - (K + lambda I) s in FP64 with rows spread
+// over the lanes, correction through the complex64 factor);
+// if the factorization breaks down or the refinement does not contract, the
+// system is solved by an FP64 Cholesky instead (counted in nref).  FP64 path
+// (double): FP64 Cholesky directly.  The slice is written row-major in FP64
+// and the compute type; then h_{m+1}(e) = h_m(e)^T Z^{m+1}(k) for the slice's
+// entries is scattered into order m+1.  A singular system keeps its old slice.
+template <typename T, int R>
+__global__ void __launch_bounds__(32 * SolveCfg<T, R>::WPB)
+k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<T>::type* __restrict__ H,
+            const int32_t* __restrict__ seg, const int32_t* __restrict__ nxt,
+            typename cvec<T>::type* __restrict__ Hn, double2* __restrict__ Zd,
+            typename cvec<T>::type* __restrict__ Zt, double2* __restrict__ fb, double lambda_in, double ridge,
+            unsigned long long* __restrict__ nsing, unsigned long long* __restrict__ nref, int S)
+{
+    typedef typename cvec<T>::type V;
+    typedef SolveCfg<T, R> C;
+    constexpr int D = C::D, NPK = C::NPK, NS = C::NS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char* base = smem + (size_t)wib * C::WBYTES;
+    V* Lm = (V*)base;
+    double2* s_d = (double2*)(base + C::LBYTES);
+    V* zt_s = (V*)(s_d + D);
+    T* sc_s = (T*)(zt_s + D);  // Jacobi scaling of the complex64 factorization
+
+    for (int k = blockIdx.x * C::WPB + wib; k < S; k += gridDim.x * C::WPB) {
+        const V* K = rec + (size_t)k * (NPK + D);
+        __syncwarp();
+        double tr = 0.0;
+        for (int p = lane; p < D; p += 32) tr += (double)K[tri(p, p)].x;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        // lambda, raised to the ridge floor (relative to the mean diagonal) when set
+        const double lambda = fmax(lambda_in, ridge * tr / D);
+        const double tol = lambda > 0.0 ? 0.0 : 1e-14 * (tr + D * lambda);
+        if constexpr (C::MIXED) {
+            // equilibrate: factor S (K + lambda I) S with S = diag(K_pp + lambda)^(-1/2)
+            for (int p = lane; p < D; p += 32) {
+                const double dp = (double)K[tri(p, p)].x + lambda;
+                sc_s[p] = dp > 0.0 ? (T)(1.0 / sqrt(dp)) : (T)1;
+            }
+            __syncwarp();
+            int rr = 0, qq = lane;
+            while (qq > rr) { qq -= rr + 1; ++rr; }
+            for (int q = lane; q < NPK; q += 32) {
+                V v = K[q];
+                if (rr == qq) v.x += (T)lambda;
+                const T f = sc_s[rr] * sc_s[qq];
+                v.x *= f;
+                v.y *= f;
+                Lm[q] = v;
+                qq += 32;
+                while (qq > rr) { qq -= rr + 1; ++rr; }
+            }
+        } else {
+            for (int q = lane; q < NPK; q += 32) Lm[q] = K[q];
+            __syncwarp();
+            for (int p = lane; p < D; p += 32) Lm[tri(p, p)].x += (T)lambda;
+        }
+        __syncwarp();
+        double2 sv[NS];
+        bool ok;
+        if constexpr (C::MIXED) {
+            bool conv = false;
+            if (warp_chol<V, T>(Lm, D, (T)tol, lane)) {
+                V bv[NS];
+                T scl[NS];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    const int p = lane + 32 * s;
+                    scl[s] = p < D ? sc_s[p] : (T)0;
+                    bv[s] = p < D ? K[NPK + p] : czero<V>();
+                    bv[s].x *= scl[s];
+                    bv[s].y *= scl[s];
+                }
+                warp_chol_solve<V, T, NS>(Lm, D, bv, lane);
+#pragma unroll
+                for (int s = 0; s < NS; ++s) sv[s] = make_double2((double)(bv[s].x * scl[s]), (double)(bv[s].y * scl[s]));
+                // FP64 copy of K for the residuals (converted once per slice)
+                double2* Kd = fb + (size_t)k * NPK;
+                for (int q = lane; q < NPK; q += 32) Kd[q] = to_d2(K[q]);
+                __syncwarp();
+                double dmax = 0.0, smax = 0.0;
+                for (int it = 0; it < 3; ++it) {
+                    // FP64 residual r = y - (K + lambda I) s, rows over the lanes
+                    __syncwarp();
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
+                        const int p = lane + 32 * s;
+                        if (p < D) s_d[p] = sv[s];
+                    }
+                    __syncwarp();
+                    double2 rv[NS];
+                    double rmax = 0.0;
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
+                        const int p = lane + 32 * s;
+                        double2 acc = make_double2(0.0, 0.0);
+                        if (p < D) {
+                            const double2 yp = to_d2(K[NPK + p]);
+                            acc.x = yp.x - lambda * sv[s].x;
+                            acc.y = yp.y - lambda * sv[s].y;
+                            for (int q = 0; q <= p; ++q) {   // K_pq s_q
+                                const double2 kk = Kd[tri(p, q)], sq = s_d[q];
+                                acc.x -= kk.x * sq.x - kk.y * sq.y;
+                                acc.y -= kk.x * sq.y + kk.y * sq.x;
+                            }
+                            for (int q = p + 1; q < D; ++q) {  // conj(K_qp) s_q
+                                const double2 kk = Kd[tri(q, p)], sq = s_d[q];
+                                acc.x -= kk.x * sq.x + kk.y * sq.y;
+                                acc.y -= kk.x * sq.y - kk.y * sq.x;
+                            }
+                        }
+                        rv[s] = acc;
+                        rmax = fmax(rmax, fmax(fabs(acc.x), fabs(acc.y)));
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+                    const double sc = rmax > 0.0 ? rmax : 1.0;
+                    const double isc = 1.0 / sc;
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
+                        bv[s] = from_d2<V>(make_double2(rv[s].x * isc, rv[s].y * isc));
+                        bv[s].x *= scl[s];
+                        bv[s].y *= scl[s];
+                    }
+                    warp_chol_solve<V, T, NS>(Lm, D, bv, lane);
+                    dmax = 0.0;
+                    smax = 0.0;
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
+                        const double dx = (double)(bv[s].x * scl[s]) * sc, dy = (double)(bv[s].y * scl[s]) * sc;
+                        sv[s].x += dx;
+                        sv[s].y += dy;
+                        dmax = fmax(dmax, fmax(fabs(dx), fabs(dy)));
+                        smax = fmax(smax, fmax(fabs(sv[s].x), fabs(sv[s].y)));
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+                        smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+                    }
+                    if (dmax <= 1e-6 * smax) break;
+                }
+                conv = dmax <= 1e-4 * smax;
+            }
+            ok = conv;
+            if (!conv) {
+                // FP64 Cholesky of the same system in the slice's FP64 record
+                double2* Kd = fb + (size_t)k * NPK;
+                __syncwarp();
+                for (int q = lane; q < NPK; q += 32) Kd[q] = to_d2(K[q]);
+                __syncwarp();
+                for (int p = lane; p < D; p += 32) Kd[tri(p, p)].x += lambda;
+                ok = warp_chol<double2, double>(Kd, D, tol, lane);
+                if (ok) {
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
+                        const int p = lane + 32 * s;
+                        sv[s] = p < D ? to_d2(K[NPK + p]) : make_double2(0.0, 0.0);
+                    }
+                    warp_chol_solve<double2, double, NS>(Kd, D, sv, lane);
+                }
+                if (lane == 0) atomicAdd(nref, 1ull);
+            }
+        } else {
+            ok = warp_chol<V, T>(Lm, D, (T)tol, lane);
             if (ok) {
-                const double2 s = x_s[q];
-                Zd[(size_t)k * D + q] = s;
-                const V st = from_d2<V>(s);
-                Zt[(size_t)k * D + q] = st;
-                zt_s[q] = st;
-            } else {
-                zt_s[q] = Zt[(size_t)k * D + q];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    const int p = lane + 32 * s;
+                    sv[s] = p < D ? to_d2(K[NPK + p]) : make_double2(0.0, 0.0);
+                }
+                warp_chol_solve<V, T, NS>(Lm, D, sv, lane);
             }
         }
-        __syncthreads();
+        if (!ok && lane == 0) atomicAdd(nsing, 1ull);
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int p = lane + 32 * s;
+            if (p < D) {
+                if (ok) {
+                    Zd[(size_t)k * D + p] = sv[s];
+                    const V st = from_d2<V>(sv[s]);
+                    Zt[(size_t)k * D + p] = st;
+                    zt_s[p] = st;
+                } else {
+                    zt_s[p] = Zt[(size_t)k * D + p];
+                }
+            }
+        }
+        __syncwarp();
         // left environment update into the next order
-        for (int p = s0 + tid; p < s1; p += nth) {
+        const int s0 = seg[k], s1 = seg[k + 1];
+        for (int p = s0 + lane; p < s1; p += 32) {
             V h[R];
 #pragma unroll
             for (int a = 0; a < R; ++a) h[a] = H[(size_t)p * R + a];

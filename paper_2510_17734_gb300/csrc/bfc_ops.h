@@ -11,6 +11,8 @@ struct Ops {
     bfc_status (*sweep)(Ctx*);
     bfc_status (*grad)(Ctx*, double2*, double*);
     bfc_status (*eval)(Ctx*, const int32_t*, const int32_t*, int64_t, double2*, const double2*, double*, int);
+    size_t (*record_bytes)(int64_t n, int64_t S);
+    size_t (*fallback_bytes)(int64_t S);
 };
 
 constexpr int MAX_RANK = 10;

@@ -15,11 +15,52 @@ template <typename T, int R> struct Path {
 
     static bfc_status configure(Ctx* c)
     {
-        typedef MidCfg<T, R> C;
-        cudaError_t e = cudaFuncSetAttribute(k_mid<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_mid_gram<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)GramCfg<T, R>::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_mid_solve<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SolveCfg<T, R>::SMEM);
         if (e != cudaSuccess)
-            return fail(c, BFC_ECUDA, std::string("cudaFuncSetAttribute(k_mid): ") + cudaGetErrorString(e));
+            return fail(c, BFC_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+        return BFC_OK;
+    }
+
+    // Bytes of the per-block normal-equation records (the larger of the
+    // middle-slice and the outer-fiber layouts) and of the FP64 fallback area.
+    static size_t record_bytes(int64_t n, int64_t S)
+    {
+        const size_t mid = (size_t)S * (GramCfg<T, R>::NPK + R * R) * sizeof(V);
+        const size_t outer = (size_t)n * (R * (R + 1) / 2 + R) * sizeof(double2);
+        return mid > outer ? mid : outer;
+    }
+    static size_t fallback_bytes(int64_t S)
+    {
+        return SolveCfg<T, R>::MIXED ? (size_t)S * SolveCfg<T, R>::NPK * sizeof(double2) : 0;
+    }
+
+    // One block-coordinate update of an outer factor (rows: S^1, cols: S^{L+2}).
+    template <bool COLS>
+    static bfc_status outer_level(Ctx* c, const V* A, int level, double2* zd, V* zt, V* Hn)
+    {
+        const int64_t n = c->n;
+        double2* rec = (double2*)c->rec;
+        {
+            ProfScope ps(c, COLS ? "outer_cols_gram" : "outer_rows_gram");
+            k_outer_gram<T, R><<<nblocks(n, 4), 128, 0, c->stream>>>(A, (const V*)c->tval[level], c->seg[level],
+                                                                      (int)n, rec);
+        }
+        {
+            ProfScope ps(c, COLS ? "outer_cols_solve" : "outer_rows_solve");
+            k_outer_solve<T, R><<<nblocks(n, 64), 64, 0, c->stream>>>(rec, (int)n, c->P.lambda, c->ridge, zd, zt,
+                                                                       c->d_count);
+        }
+        {
+            ProfScope ps(c, COLS ? "outer_cols_post" : "outer_rows_post");
+            k_outer_post<T, R, COLS><<<nblocks(n, 4), 128, 0, c->stream>>>(
+                A, (const V*)c->tval[level], c->seg[level], (int)n, zt, COLS ? nullptr : c->nxt[0], Hn,
+                COLS ? c->d_red : nullptr);
+        }
+        BFC_LAUNCH_CHECK(c, "outer level");
         return BFC_OK;
     }
 
@@ -48,41 +89,38 @@ template <typename T, int R> struct Path {
     // One ALS sweep (Alg. 1) + training residual partials (per column fiber).
     static bfc_status sweep(Ctx* c)
     {
-        typedef MidCfg<T, R> C;
-        const int64_t NR = c->N * R, S = c->S, n = c->n;
+        const int64_t NR = c->N * R, S = c->S;
         const int L = c->L;
         V* W = (V*)c->W;
         V* H0 = (V*)c->H[0];
         V* H1 = (V*)c->H[1];
         BFC_TRY(right_envs(c));
-        {
-            ProfScope ps(c, "outer_rows");
-            k_outer<T, R, false><<<nblocks(n, 4), 128, 0, c->stream>>>(
-                W, (const V*)c->tval[0], c->seg[0], (int)n, c->P.lambda, c->z1d, (V*)c->z1t, c->nxt[0], H0,
-                nullptr, c->d_count);
-        }
-        BFC_LAUNCH_CHECK(c, "outer_rows");
+        BFC_TRY(outer_level<false>(c, W, 0, c->z1d, (V*)c->z1t, H0));
+        typedef GramCfg<T, R> GC;
+        typedef SolveCfg<T, R> SC;
+        const unsigned gsolve = (unsigned)((S + SC::WPB - 1) / SC::WPB);
         for (int m = 1; m <= L; ++m) {
             V* hin = (m - 1) & 1 ? H1 : H0;
             V* hout = m & 1 ? H1 : H0;
-            ProfScope ps(c, "mid_gram_solve");
-            k_mid<T, R><<<(unsigned)S, C::NTH, C::SMEM, c->stream>>>(
-                hin, W + (size_t)m * NR, (const V*)c->tval[m], c->seg[m], c->nxt[m], hout,
-                c->Zd + (size_t)(m - 1) * S * R * R, (V*)c->Zt + (size_t)(m - 1) * S * R * R, c->P.lambda,
-                c->d_count, (int)S);
+            {
+                ProfScope ps(c, "mid_gram");
+                k_mid_gram<T, R><<<(unsigned)S, GC::NTH, GC::SMEM, c->stream>>>(
+                    hin, W + (size_t)m * NR, (const V*)c->tval[m], c->seg[m], (V*)c->rec, (int)S);
+            }
+            {
+                ProfScope ps(c, "mid_solve");
+                k_mid_solve<T, R><<<gsolve, 32 * SC::WPB, SC::SMEM, c->stream>>>(
+                    (const V*)c->rec, hin, c->seg[m], c->nxt[m], hout, c->Zd + (size_t)(m - 1) * S * R * R,
+                    (V*)c->Zt + (size_t)(m - 1) * S * R * R, c->fb, c->P.lambda, c->ridge, c->d_count,
+                    c->d_count + 1, (int)S);
+            }
         }
-        BFC_LAUNCH_CHECK(c, "mid_gram_solve");
+        BFC_LAUNCH_CHECK(c, "middle levels");
         V* hc = L & 1 ? H1 : H0;
-        {
-            ProfScope ps(c, "outer_cols");
-            k_outer<T, R, true><<<nblocks(n, 4), 128, 0, c->stream>>>(
-                hc, (const V*)c->tval[L + 1], c->seg[L + 1], (int)n, c->P.lambda, c->zLd, (V*)c->zLt, nullptr,
-                nullptr, c->d_red, c->d_count);
-        }
-        BFC_LAUNCH_CHECK(c, "outer_cols");
+        BFC_TRY(outer_level<true>(c, hc, L + 1, c->zLd, (V*)c->zLt, nullptr));
         {
             ProfScope ps(c, "reduce");
-            launch_reduce_pairs(c->d_red, n, c->d_scalars + 0, c->stream);
+            launch_reduce_pairs(c->d_red, c->n, c->d_scalars + 0, c->stream);
         }
         BFC_LAUNCH_CHECK(c, "reduce");
         return BFC_OK;
