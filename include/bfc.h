@@ -109,6 +109,7 @@ typedef struct {
     double entries_per_s;   /* training entries / sweep time                 */
     int64_t singular_slices;/* systems left unchanged (Cholesky breakdown)   */
     int64_t refined_fallbacks; /* precision form: FP64 Cholesky fallbacks    */
+    int64_t refine_steps;   /* precision form: FP64 refinement steps taken   */
 } bfc_sweep_stats;
 
 typedef struct {

@@ -61,7 +61,8 @@ class SweepStats(ctypes.Structure):
     _fields_ = [("sweep", ctypes.c_int32), ("train_rel_err", ctypes.c_double),
                 ("test_rel_err", ctypes.c_double), ("objective", ctypes.c_double),
                 ("sweep_ms", ctypes.c_double), ("entries_per_s", ctypes.c_double),
-                ("singular_slices", ctypes.c_int64), ("refined_fallbacks", ctypes.c_int64)]
+                ("singular_slices", ctypes.c_int64), ("refined_fallbacks", ctypes.c_int64),
+                ("refine_steps", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -290,7 +290,10 @@ static bfc_status build(Ctx* c, const Inputs& in)
     const Ops* ops = get_ops(c->fp32, r);
     BFC_TRY(dalloc(c, &c->rec, ops->record_bytes(n, S), "normal-equation records"));
     const size_t fbb = ops->fallback_bytes(S);
-    if (fbb > 0 && L > 0) BFC_TRY(dalloc(c, (void**)&c->fb, fbb, "FP64 fallback"));
+    if (fbb > 0 && L > 0) {
+        BFC_TRY(dalloc(c, (void**)&c->fb, fbb, "FP64 refinement records"));
+        BFC_TRY(dalloc(c, (void**)&c->fblist, (size_t)S * sizeof(int32_t), "fallback list"));
+    }
     BFC_TRY(ops->configure(c));
     return sync(c);
 }
@@ -338,9 +341,9 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
 static bfc_status collect_stats(Ctx* c, bfc_sweep_stats* out, float ms)
 {
     double hs[8];
-    unsigned long long hc[2];
+    unsigned long long hc[3];
     BFC_CK(c, cudaMemcpyAsync(hs, c->d_scalars, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    BFC_CK(c, cudaMemcpyAsync(hc, c->d_count, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    BFC_CK(c, cudaMemcpyAsync(hc, c->d_count, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
     BFC_TRY(sync(c));
     if (out) {
         out->sweep = c->sweeps_done;
@@ -351,6 +354,7 @@ static bfc_status collect_stats(Ctx* c, bfc_sweep_stats* out, float ms)
         out->entries_per_s = ms > 0 ? (double)c->N / (ms * 1e-3) : 0.0;
         out->singular_slices = (int64_t)hc[0];
         out->refined_fallbacks = (int64_t)hc[1];
+        out->refine_steps = (int64_t)hc[2];
     }
     if (!isfinite(hs[0])) return fail(c, BFC_ENONFINITE, "training residual is not finite");
     return BFC_OK;
@@ -373,7 +377,7 @@ static bfc_status test_error(Ctx* c, int slot)
 static bfc_status sweep_impl(Ctx* c, bfc_sweep_stats* out)
 {
     const Ops* ops = get_ops(c->fp32, c->r);
-    BFC_CK(c, cudaMemsetAsync(c->d_count, 0, 2 * sizeof(unsigned long long), c->stream));
+    BFC_CK(c, cudaMemsetAsync(c->d_count, 0, 3 * sizeof(unsigned long long), c->stream));
     BFC_CK(c, cudaEventRecord(c->ev0, c->stream));
     BFC_TRY(ops->sweep(c));
     BFC_TRY(factor_sumsq(c, 2));

@@ -58,7 +58,8 @@ struct Ctx {
     void* H[2] = {nullptr, nullptr};
     void* Rres[2] = {nullptr, nullptr};  // residual carried along the orders (gradient)
     void* rec = nullptr;              // per-block normal-equation records [K packed | y]
-    double2* fb = nullptr;            // FP64 fallback factors (precision form)
+    double2* fb = nullptr;            // FP64 refinement / fallback records (precision form)
+    int32_t* fblist = nullptr;        // slices handed to the FP64 fallback in the current level
 
     // factors: FP64 master and compute-type copies (alias when double)
     double2 *z1d = nullptr, *Zd = nullptr, *zLd = nullptr;
@@ -68,7 +69,10 @@ struct Ctx {
     double* d_red = nullptr;          // partial sums, size red_cap
     int64_t red_cap = 0;
     double* d_scalars = nullptr;      // 16 doubles of results
-    unsigned long long* d_count = nullptr;  // 8 counters
+    // 8 counters: [0] singular systems, [1] FP64 fallbacks and [2] refinement
+    // steps of the sweep, [3] fallback list length of the current level,
+    // [4] index-check flag of bfc_eval
+    unsigned long long* d_count = nullptr;
     void* d_tmp = nullptr;            // growable scratch (eval inputs, etc.)
     size_t tmp_cap = 0;
 

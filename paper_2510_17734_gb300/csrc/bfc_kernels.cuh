@@ -159,6 +159,32 @@ template <typename E> __device__ __forceinline__ void csub_mul_conj(E& acc, E a,
     acc.y -= a.y * b.x - a.x * b.y;
 }
 
+// Error-free transformations (Knuth TwoSum, FMA-based TwoProd) for
+// double-float ("hi + lo" float pair, about 48 significant bits) arithmetic
+// on the FP32 pipes.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// acc -= k * (sh + sl) for complex k (float) and a double-float complex s;
+// acc = {re_hi, re_lo, im_hi, im_lo}.
+__device__ __forceinline__ void df_sub_cmul(float4& acc, float2 k, float2 sh, float2 sl)
+{
+    float t, e;
+    const float p1 = k.x * sh.x, e1 = fmaf(k.x, sh.x, -p1);
+    const float p2 = k.y * sh.y, e2 = fmaf(k.y, sh.y, -p2);
+    two_sum(acc.x, -p1, t, e); acc.x = t; acc.y += e;
+    two_sum(acc.x, p2, t, e); acc.x = t; acc.y += e;
+    acc.y -= e1 - e2 + (k.x * sl.x - k.y * sl.y);
+    const float p3 = k.x * sh.y, e3 = fmaf(k.x, sh.y, -p3);
+    const float p4 = k.y * sh.x, e4 = fmaf(k.y, sh.x, -p4);
+    two_sum(acc.z, -p3, t, e); acc.z = t; acc.w += e;
+    two_sum(acc.z, -p4, t, e); acc.z = t; acc.w += e;
+    acc.w -= e3 + e4 + (k.x * sl.y + k.y * sl.x);
+}
+
 // Hermitian Cholesky + two triangular solves for one small system held by one
 // thread (R compile-time: the loops unroll and K, y stay in registers).
 // K: packed lower (R(R+1)/2), y: right-hand side, overwritten by the solution.
@@ -376,54 +402,75 @@ k_outer_post(const typename cvec<T>::type* __restrict__ A, const typename cvec<T
 }
 
 // ------------------------------------------------------------------------
-// Middle level m, stage 1 (Gram): one CTA per slice k of S^{m+1}.
+// Middle level m, stage 1 (Gram): one CTA per slice k of S^{m+1}
+// (persistent over slices).
 //   a_e = h_m(e) (x) w_m(e), a[p r + c] = h_p w_c, K = sum conj(a) a^T,
 //   y = sum conj(a) t over the slice's entries (Alg. 1 middle branch).
-// Threads own 4x4 complex tiles of the lower triangle of K; entries are
-// staged in shared memory in chunks of CE and split over G thread groups.  In
-// float every chunk partial (registers) is folded into a Kahan-compensated
-// running sum (sum in registers, compensation in shared memory, so several
-// CTAs fit on one SM).  Output record per slice: [K packed | y] in the compute
-// type (the compensated sums rounded once).
+// Threads own 4x4 complex tiles of the lower triangle of K (split over G
+// entry groups for small ranks); the diagonal-tile threads also accumulate y.
+// Software pipeline over chunks of CE entries with one barrier per chunk:
+// while chunk c is multiplied out of one design-vector buffer, chunk c+1 is
+// formed into the other from its staged h, w, t, and chunk c+2 is fetched
+// into the other staging buffer with cp.async.  In float every FOLD chunks
+// the register partials are folded into Kahan-compensated running sums
+// (sums in registers, compensation in shared memory).
+// Output record per slice: [K packed lower | y] in the compute type.
 template <typename T, int R> struct GramCfg {
     static constexpr int D = R * R;
     static constexpr int DP = (D + 3) / 4 * 4;
     static constexpr int NB = DP / 4;
     static constexpr int NT = NB * (NB + 1) / 2;
-    static constexpr int CE = (DP <= 64) ? 64 : 32;
+    static constexpr int CE = 32;
     static constexpr int GT = (160 / NT) < 1 ? 1 : (160 / NT);
     static constexpr int G = GT > CE ? CE : GT;
     static constexpr int NTH = ((NT * G + 31) / 32) * 32;
+    static constexpr int FOLD = 2;
     static constexpr bool COMP = sizeof(T) == 4;
     static constexpr int NPK = D * (D + 1) / 2;
-    static constexpr int CSTRIDE = 40;  // compensation floats per worker thread
+    static constexpr int CSTRIDE = 40;  // compensation floats per thread (32 K + 8 y)
     static constexpr size_t VS = sizeof(typename cvec<T>::type);
+    static constexpr size_t RING = 2 * (size_t)CE * DP * VS + 2 * (size_t)CE * VS;  // a and t rings
+    static constexpr size_t STAGE1 = ((2 * (size_t)CE * R + CE) * VS + 15) / 16 * 16;
     static constexpr size_t CBYTES = COMP ? (size_t)NTH * CSTRIDE * sizeof(float) : 0;
     static constexpr size_t KBYTES = G > 1 ? (size_t)(NPK + D) * sizeof(double2) : 0;
     static constexpr size_t UBYTES = ((CBYTES > KBYTES ? CBYTES : KBYTES) + 15) / 16 * 16;
-    static constexpr size_t SMEM = 2 * (size_t)CE * R * VS + (size_t)CE * DP * VS + (size_t)CE * VS + UBYTES + 16;
+    static constexpr size_t SMEM = RING + 2 * STAGE1 + UBYTES + 16;
+    static constexpr int MINB0 = 65536 / (NTH * 128);
+    static constexpr int MINB = MINB0 < 1 ? 1 : (MINB0 > 3 ? 3 : MINB0);
 };
 
+// Asynchronous global -> shared copy of one complex value (8 or 16 bytes).
+__device__ __forceinline__ void cp_async_v(float2* smem_dst, const float2* gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_v(double2* smem_dst, const double2* gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <typename T, int R>
-__global__ void __launch_bounds__(GramCfg<T, R>::NTH)
+__global__ void __launch_bounds__(GramCfg<T, R>::NTH, GramCfg<T, R>::MINB)
 k_mid_gram(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>::type* __restrict__ Wm,
            const typename cvec<T>::type* __restrict__ tv, const int32_t* __restrict__ seg,
            typename cvec<T>::type* __restrict__ rec, int S)
 {
     typedef typename cvec<T>::type V;
     typedef GramCfg<T, R> C;
-    constexpr int D = C::D, DP = C::DP, NPK = C::NPK;
+    constexpr int D = C::D, DP = C::DP, NPK = C::NPK, CE = C::CE, NTH = C::NTH;
     extern __shared__ __align__(16) unsigned char smem[];
-    V* h_s = (V*)smem;
-    V* w_s = h_s + C::CE * R;
-    V* a_s = w_s + C::CE * R;
-    V* t_s = a_s + C::CE * DP;
-    unsigned char* U = (unsigned char*)(t_s + C::CE);
-    float* c_s = (float*)U;
-    double2* Kacc = (double2*)U;
+    V* ring = (V*)smem;                                      // [2][CE][DP]
+    V* tring = ring + 2 * CE * DP;                           // [2][CE]
+    unsigned char* stage_base = smem + C::RING;              // 2 x { h [CE][R], w [CE][R], t [CE] }
+    unsigned char* U = stage_base + 2 * C::STAGE1;
+    float* c_s = (float*)U;                                  // compensation [CSTRIDE][NTH]
+    double2* Kacc = (double2*)U;                             // group reduction (G > 1)
 
     const int tid = threadIdx.x;
-    const int nth = blockDim.x;
     const bool worker = tid < C::NT * C::G;
     const int grp = tid / C::NT, tile = tid - (tid / C::NT) * C::NT;
     int I = 0;
@@ -431,8 +478,36 @@ k_mid_gram(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
     const int J = tile - I * (I + 1) / 2;
     const bool diag = (I == J);
 
+    // fetch chunk (base, cnt) of the current slice into staging buffer sb
+    auto fetch = [&](int sb, int base, int cnt) {
+        V* hs = (V*)(stage_base + sb * C::STAGE1);
+        V* ws = hs + CE * R;
+        V* ts = ws + CE * R;
+        for (int q = tid; q < cnt * R; q += NTH) {
+            cp_async_v(hs + q, H + (size_t)base * R + q);
+            cp_async_v(ws + q, Wm + (size_t)base * R + q);
+        }
+        for (int e = tid; e < cnt; e += NTH) cp_async_v(ts + e, tv + base + e);
+        cp_async_commit();
+    };
+    // form the design vectors (and copy t) of staging buffer sb into ring buffer rb
+    auto form = [&](int sb, int rb, int cnt) {
+        const V* hs = (const V*)(stage_base + sb * C::STAGE1);
+        const V* ws = hs + CE * R;
+        const V* ts = ws + CE * R;
+        V* buf = ring + (size_t)rb * CE * DP;
+        for (int idx = tid; idx < CE * DP; idx += NTH) {
+            const int e = idx / DP, q = idx - e * DP;
+            V a = czero<V>();
+            if (q < D && e < cnt) a = cmul(hs[e * R + q / R], ws[e * R + q % R]);
+            buf[idx] = a;
+        }
+        for (int e = tid; e < CE; e += NTH) tring[rb * CE + e] = e < cnt ? ts[e] : czero<V>();
+    };
+
     for (int k = blockIdx.x; k < S; k += gridDim.x) {
         const int s0 = seg[k], s1 = seg[k + 1];
+        const int nch = (s1 - s0 + CE - 1) / CE;
         V acc[4][4], sum[4][4], yacc[4], ysum[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -441,32 +516,33 @@ k_mid_gram(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
 #pragma unroll
             for (int v = 0; v < 4; ++v) { acc[u][v] = czero<V>(); sum[u][v] = czero<V>(); }
         }
-        __syncthreads();  // previous slice done with the shared buffers
+        __syncthreads();  // previous slice done with every shared buffer
         if (C::COMP && worker)
-            for (int x = 0; x < C::CSTRIDE; ++x) c_s[x * C::NTH + tid] = 0.0f;
-
-        for (int base = s0; base < s1; base += C::CE) {
-            const int cnt = min(C::CE, s1 - base);
+            for (int x = 0; x < C::CSTRIDE; ++x) c_s[x * NTH + tid] = 0.0f;
+        // prologue: chunk 0 staged and formed, chunk 1 in flight
+        if (nch > 0) {
+            fetch(0, s0, min(CE, s1 - s0));
+            cp_async_wait_all();
             __syncthreads();
-            for (int q = tid; q < cnt * R; q += nth) {
-                h_s[q] = H[(size_t)base * R + q];
-                w_s[q] = Wm[(size_t)base * R + q];
+            form(0, 0, min(CE, s1 - s0));
+            if (nch > 1) fetch(1, s0 + CE, min(CE, s1 - s0 - CE));
+        }
+        int pend = 0;
+        for (int c = 0; c < nch; ++c) {
+            const int base = s0 + c * CE;
+            const int cnt = min(CE, s1 - base);
+            // chunk c formed (ring c&1) and chunk c+1 staged (stage (c+1)&1) by everybody
+            cp_async_wait_all();
+            __syncthreads();
+            if (c + 1 < nch) {
+                form((c + 1) & 1, (c + 1) & 1, min(CE, s1 - base - CE));
+                if (c + 2 < nch) fetch(c & 1, base + 2 * CE, min(CE, s1 - base - 2 * CE));
             }
-            for (int e = tid; e < cnt; e += nth) t_s[e] = tv[base + e];
-            __syncthreads();
-            for (int idx = tid; idx < cnt * DP; idx += nth) {
-                const int e = idx / DP, q = idx - e * DP;
-                V a = czero<V>();
-                if (q < D) {
-                    const int pa = q / R, pc = q - pa * R;
-                    a = cmul(h_s[e * R + pa], w_s[e * R + pc]);
-                }
-                a_s[idx] = a;
-            }
-            __syncthreads();
             if (worker) {
+                const V* buf = ring + (size_t)(c & 1) * CE * DP;
+                const V* ts = tring + (c & 1) * CE;
                 for (int e = grp; e < cnt; e += C::G) {
-                    const V* ae = a_s + e * DP;
+                    const V* ae = buf + e * DP;
                     V ap[4], aq[4];
                     load4(ap, ae + I * 4);
                     load4(aq, ae + J * 4);
@@ -475,19 +551,20 @@ k_mid_gram(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
 #pragma unroll
                         for (int v = 0; v < 4; ++v) cmacc(acc[u][v], ap[u], aq[v]);
                     if (diag) {
-                        const V te = t_s[e];
+                        const V te = ts[e];
 #pragma unroll
                         for (int u = 0; u < 4; ++u) cmacc(yacc[u], ap[u], te);
                     }
                 }
-                if (C::COMP) {
+                if (C::COMP && (++pend == C::FOLD || c + 1 == nch)) {
+                    pend = 0;
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
                             float sx = (float)sum[u][v].x, sy = (float)sum[u][v].y;
-                            float& cx = c_s[(2 * (u * 4 + v)) * C::NTH + tid];
-                            float& cy = c_s[(2 * (u * 4 + v) + 1) * C::NTH + tid];
+                            float& cx = c_s[(2 * (u * 4 + v)) * NTH + tid];
+                            float& cy = c_s[(2 * (u * 4 + v) + 1) * NTH + tid];
                             kahan(sx, cx, (float)acc[u][v].x);
                             kahan(sy, cy, (float)acc[u][v].y);
                             sum[u][v].x = sx; sum[u][v].y = sy;
@@ -495,8 +572,8 @@ k_mid_gram(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
                         }
                         if (diag) {
                             float sx = (float)ysum[u].x, sy = (float)ysum[u].y;
-                            float& cx = c_s[(32 + 2 * u) * C::NTH + tid];
-                            float& cy = c_s[(32 + 2 * u + 1) * C::NTH + tid];
+                            float& cx = c_s[(32 + 2 * u) * NTH + tid];
+                            float& cy = c_s[(32 + 2 * u + 1) * NTH + tid];
                             kahan(sx, cx, (float)yacc[u].x);
                             kahan(sy, cy, (float)yacc[u].y);
                             ysum[u].x = sx; ysum[u].y = sy;
@@ -506,18 +583,17 @@ k_mid_gram(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
                 }
             }
         }
-        __syncthreads();
         if (C::COMP && worker) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
-                    acc[u][v].x = sum[u][v].x - c_s[(2 * (u * 4 + v)) * C::NTH + tid];
-                    acc[u][v].y = sum[u][v].y - c_s[(2 * (u * 4 + v) + 1) * C::NTH + tid];
+                    acc[u][v].x = sum[u][v].x - c_s[(2 * (u * 4 + v)) * NTH + tid];
+                    acc[u][v].y = sum[u][v].y - c_s[(2 * (u * 4 + v) + 1) * NTH + tid];
                 }
                 if (diag) {
-                    yacc[u].x = ysum[u].x - c_s[(32 + 2 * u) * C::NTH + tid];
-                    yacc[u].y = ysum[u].y - c_s[(32 + 2 * u + 1) * C::NTH + tid];
+                    yacc[u].x = ysum[u].x - c_s[(32 + 2 * u) * NTH + tid];
+                    yacc[u].y = ysum[u].y - c_s[(32 + 2 * u + 1) * NTH + tid];
                 }
             }
         }
@@ -539,7 +615,7 @@ k_mid_gram(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
             }
         } else {
             __syncthreads();  // compensation reads done before Kacc overwrites them
-            for (int q = tid; q < NPK + D; q += nth) Kacc[q] = make_double2(0.0, 0.0);
+            for (int q = tid; q < NPK + D; q += NTH) Kacc[q] = make_double2(0.0, 0.0);
             __syncthreads();
             for (int g = 0; g < C::G; ++g) {  // deterministic order over the groups
                 if (worker && grp == g) {
@@ -564,51 +640,108 @@ k_mid_gram(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
                 }
                 __syncthreads();
             }
-            for (int q = tid; q < NPK + D; q += nth) out[q] = from_d2<V>(Kacc[q]);
+            for (int q = tid; q < NPK + D; q += NTH) out[q] = from_d2<V>(Kacc[q]);
         }
     }
 }
 
 // ------------------------------------------------------------------------
+// Row of slot s owned by a lane in the warp-level factorization: even slots
+// take rows 32 s + lane, odd slots mirror them (32 s + 31 - lane), so the two
+// rows of a lane have complementary lengths and the work per lane is balanced.
+__device__ __forceinline__ int owned_row(int s, int lane) { return 32 * s + ((s & 1) ? 31 - lane : lane); }
+
 // Warp-level Hermitian Cholesky (K = L L^H) of a D x D packed lower matrix
-// in shared or global memory.  Right-looking; the trailing update of each
-// column is flattened over all (row, col) pairs so every lane has work.  The
-// diagonal of L is real, so its imaginary slot stores 1 / L_cc for the
+// in shared or global memory, right-looking and blocked by NBK columns:
+//  (1) the NBK x NBK diagonal block is factored column by column;
+//  (2) every panel row r below it, owned by one lane, is solved in registers:
+//      L[r][j0..j1) = K[r][j0..j1) L_dd^{-H};
+//  (3) the trailing matrix gets the rank-NBK update
+//      L[r][q] -= sum_k L[r][j0+k] conj(L[q][j0+k]), the lane holding its
+//      panel row in registers while all lanes read the same panel row q.
+// The diagonal of L is real, so its imaginary slot stores 1 / L_cc for the
 // triangular solves.  Returns false (warp-uniform) when a pivot is <= tol.
-template <typename E, typename S>
+template <typename E, typename S, int NS>
 __device__ bool warp_chol(E* Lm, int D, S tol, int lane)
 {
-    for (int c = 0; c < D; ++c) {
-        __syncwarp();
-        const S d = Lm[tri(c, c)].x;
-        if (!(d > tol)) return false;
-        const S piv = sqrt(d), inv = S(1) / piv;
-        __syncwarp();
-        if (lane == 0) {
-            E v;
-            v.x = piv;
-            v.y = inv;  // the factor's diagonal is real: its imaginary slot keeps 1 / L_cc
-            Lm[tri(c, c)] = v;
+    constexpr int NBK = 8;
+    for (int j0 = 0; j0 < D; j0 += NBK) {
+        const int j1 = min(j0 + NBK, D);
+        // (1) diagonal block
+        for (int c = j0; c < j1; ++c) {
+            __syncwarp();
+            const S d = Lm[tri(c, c)].x;
+            if (!(d > tol)) return false;
+            const S piv = sqrt(d), inv = S(1) / piv;
+            __syncwarp();
+            if (lane == 0) {
+                E v;
+                v.x = piv;
+                v.y = inv;
+                Lm[tri(c, c)] = v;
+            }
+            const int r = c + 1 + lane;
+            if (r < j1) {
+                E l = Lm[tri(r, c)];
+                l.x *= inv;
+                l.y *= inv;
+                Lm[tri(r, c)] = l;
+            }
+            __syncwarp();
+            if (r < j1) {
+                const E a = Lm[tri(r, c)];
+                for (int q = c + 1; q <= r; ++q) {
+                    E cur = Lm[tri(r, q)];
+                    csub_mul_conj(cur, a, Lm[tri(q, c)]);
+                    Lm[tri(r, q)] = cur;
+                }
+            }
         }
-        for (int row = c + 1 + lane; row < D; row += 32) {
-            E l = Lm[tri(row, c)];
-            l.x *= inv;
-            l.y *= inv;
-            Lm[tri(row, c)] = l;
+        __syncwarp();
+        if (j1 >= D) break;
+        const int nb = j1 - j0;
+        // (2) panel rows, solved in registers by their owner lanes
+        E x[NS][NBK];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int r = owned_row(s, lane);
+            if (r >= j1 && r < D) {
+                const E* rowp = Lm + tri(r, 0);
+#pragma unroll
+                for (int k = 0; k < NBK; ++k) x[s][k] = k < nb ? rowp[j0 + k] : E{};
+#pragma unroll
+                for (int cc = 0; cc < NBK; ++cc) {
+                    if (cc < nb) {
+                        const E* drow = Lm + tri(j0 + cc, 0);
+#pragma unroll
+                        for (int k = 0; k < cc; ++k) csub_mul_conj(x[s][cc], x[s][k], drow[j0 + k]);
+                        const S inv = drow[j0 + cc].y;
+                        x[s][cc].x *= inv;
+                        x[s][cc].y *= inv;
+                    }
+                }
+                E* roww = Lm + tri(r, 0);
+#pragma unroll
+                for (int k = 0; k < NBK; ++k)
+                    if (k < nb) roww[j0 + k] = x[s][k];
+            }
         }
         __syncwarp();
-        const int m = D - c - 1;
-        const int npairs = m * (m + 1) / 2;
-        int rr = 0, qq = lane;
-        while (rr < m && qq > rr) { qq -= rr + 1; ++rr; }
-        for (int idx = lane; idx < npairs; idx += 32) {
-            const int r_ = c + 1 + rr, q_ = c + 1 + qq;
-            const E a = Lm[tri(r_, c)], bq = Lm[tri(q_, c)];
-            E cur = Lm[tri(r_, q_)];
-            csub_mul_conj(cur, a, bq);
-            Lm[tri(r_, q_)] = cur;
-            qq += 32;
-            while (rr < m && qq > rr) { qq -= rr + 1; ++rr; }
+        // (3) rank-NBK trailing update
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int r = owned_row(s, lane);
+            if (r >= j1 && r < D) {
+                E* rowp = Lm + tri(r, 0);
+                for (int q = j1; q <= r; ++q) {
+                    const E* qrow = Lm + tri(q, 0) + j0;
+                    E cur = rowp[q];
+#pragma unroll
+                    for (int k = 0; k < NBK; ++k)
+                        if (k < nb) csub_mul_conj(cur, x[s][k], qrow[k]);
+                    rowp[q] = cur;
+                }
+            }
         }
     }
     __syncwarp();
@@ -668,6 +801,29 @@ __device__ __forceinline__ void warp_chol_solve(const E* Lm, int D, E (&bv)[NS],
     }
 }
 
+// Left environment update of slice k: h_{m+1}(e) = h_m(e)^T Z^{m+1}(k) for the
+// slice's entries (lanes over entries), scattered into order m+1.
+template <typename T, int R>
+__device__ __forceinline__ void slice_h_update(const typename cvec<T>::type* __restrict__ H,
+                                               const typename cvec<T>::type* zt_s, const int32_t* __restrict__ nxt,
+                                               typename cvec<T>::type* __restrict__ Hn, int s0, int s1, int lane)
+{
+    typedef typename cvec<T>::type V;
+    for (int p = s0 + lane; p < s1; p += 32) {
+        V h[R];
+#pragma unroll
+        for (int a = 0; a < R; ++a) h[a] = H[(size_t)p * R + a];
+        const size_t o = (size_t)nxt[p] * R;
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+            V acc2 = czero<V>();
+#pragma unroll
+            for (int a = 0; a < R; ++a) cmac(acc2, h[a], zt_s[a * R + c]);
+            Hn[o + c] = acc2;
+        }
+    }
+}
+
 template <typename T, int R> struct SolveCfg {
     static constexpr int D = R * R;
     static constexpr int NPK = D * (D + 1) / 2;
@@ -682,6 +838,9 @@ template <typename T, int R> struct SolveCfg {
     static constexpr int WPB0 = (int)((96 * 1024) / WBYTES);
     static constexpr int WPB = WPB0 < 1 ? 1 : (WPB0 > 4 ? 4 : WPB0);
     static constexpr size_t SMEM = WBYTES * WPB;
+    // CTAs per SM the register budget of k_mid_solve targets (bounded by shared memory)
+    static constexpr int MINB0 = (int)((227 * 1024) / SMEM);
+    static constexpr int MINB = MINB0 < 1 ? 1 : (MINB0 > 3 ? 3 : MINB0);
 };
 
 // Middle level m, stage 2 (solve + left update): one warp per slice.
@@ -695,13 +854,15 @@ template <typename T, int R> struct SolveCfg {
 // and the compute type; then h_{m+1}(e) = h_m(e)^T Z^{m+1}(k) for the slice's
 // entries is scattered into order m+1.  A singular system keeps its old slice.
 template <typename T, int R>
-__global__ void __launch_bounds__(32 * SolveCfg<T, R>::WPB)
+__global__ void __launch_bounds__(32 * SolveCfg<T, R>::WPB, SolveCfg<T, R>::MINB)
 k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<T>::type* __restrict__ H,
             const int32_t* __restrict__ seg, const int32_t* __restrict__ nxt,
             typename cvec<T>::type* __restrict__ Hn, double2* __restrict__ Zd,
             typename cvec<T>::type* __restrict__ Zt, double2* __restrict__ fb, double lambda_in, double ridge,
-            unsigned long long* __restrict__ nsing, unsigned long long* __restrict__ nref, int S)
+            unsigned long long* __restrict__ nsing, unsigned long long* __restrict__ nfb,
+            unsigned long long* __restrict__ nsteps, int32_t* __restrict__ fblist, int S)
 {
+    // nfb: slices handed to the FP64 fallback (length of fblist); nsteps: FP64 refinement steps
     typedef typename cvec<T>::type V;
     typedef SolveCfg<T, R> C;
     constexpr int D = C::D, NPK = C::NPK, NS = C::NS;
@@ -723,28 +884,32 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
         // lambda, raised to the ridge floor (relative to the mean diagonal) when set
         const double lambda = fmax(lambda_in, ridge * tr / D);
         const double tol = lambda > 0.0 ? 0.0 : 1e-14 * (tr + D * lambda);
+        for (int q = lane; q < NPK; q += 32) Lm[q] = K[q];
+        __syncwarp();
         if constexpr (C::MIXED) {
             // equilibrate: factor S (K + lambda I) S with S = diag(K_pp + lambda)^(-1/2)
             for (int p = lane; p < D; p += 32) {
-                const double dp = (double)K[tri(p, p)].x + lambda;
-                sc_s[p] = dp > 0.0 ? (T)(1.0 / sqrt(dp)) : (T)1;
+                const T dp = Lm[tri(p, p)].x + (T)lambda;
+                sc_s[p] = dp > (T)0 ? rsqrt(dp) : (T)1;
             }
             __syncwarp();
-            int rr = 0, qq = lane;
-            while (qq > rr) { qq -= rr + 1; ++rr; }
-            for (int q = lane; q < NPK; q += 32) {
-                V v = K[q];
-                if (rr == qq) v.x += (T)lambda;
-                const T f = sc_s[rr] * sc_s[qq];
-                v.x *= f;
-                v.y *= f;
-                Lm[q] = v;
-                qq += 32;
-                while (qq > rr) { qq -= rr + 1; ++rr; }
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int r = owned_row(s, lane);
+                if (r < D) {
+                    V* rowp = Lm + tri(r, 0);
+                    const T sr = sc_s[r];
+                    for (int q = 0; q <= r; ++q) {
+                        V v = rowp[q];
+                        if (q == r) v.x += (T)lambda;
+                        const T f = sr * sc_s[q];
+                        v.x *= f;
+                        v.y *= f;
+                        rowp[q] = v;
+                    }
+                }
             }
         } else {
-            for (int q = lane; q < NPK; q += 32) Lm[q] = K[q];
-            __syncwarp();
             for (int p = lane; p < D; p += 32) Lm[tri(p, p)].x += (T)lambda;
         }
         __syncwarp();
@@ -752,7 +917,7 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
         bool ok;
         if constexpr (C::MIXED) {
             bool conv = false;
-            if (warp_chol<V, T>(Lm, D, (T)tol, lane)) {
+            if (warp_chol<V, T, NS>(Lm, D, (T)tol, lane)) {
                 V bv[NS];
                 T scl[NS];
 #pragma unroll
@@ -764,97 +929,94 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
                     bv[s].y *= scl[s];
                 }
                 warp_chol_solve<V, T, NS>(Lm, D, bv, lane);
+                // solution as a double-float pair (hi, lo) per component
+                float2 sh[NS], sl[NS];
 #pragma unroll
-                for (int s = 0; s < NS; ++s) sv[s] = make_double2((double)(bv[s].x * scl[s]), (double)(bv[s].y * scl[s]));
-                // FP64 copy of K for the residuals (converted once per slice)
-                double2* Kd = fb + (size_t)k * NPK;
-                for (int q = lane; q < NPK; q += 32) Kd[q] = to_d2(K[q]);
-                __syncwarp();
-                double dmax = 0.0, smax = 0.0;
+                for (int s = 0; s < NS; ++s) {
+                    sh[s] = make_float2(bv[s].x * scl[s], bv[s].y * scl[s]);
+                    sl[s] = make_float2(0.f, 0.f);
+                }
+                float4* s_df = reinterpret_cast<float4*>(s_d);  // {re_hi, im_hi, re_lo, im_lo} per row
+                const float lamf = (float)lambda;
+                float dmax = 0.f, smax = 0.f;
                 for (int it = 0; it < 3; ++it) {
-                    // FP64 residual r = y - (K + lambda I) s, rows over the lanes
+                    // residual r = y - (K + lambda I) s in double-float arithmetic, rows over the lanes
                     __syncwarp();
 #pragma unroll
                     for (int s = 0; s < NS; ++s) {
                         const int p = lane + 32 * s;
-                        if (p < D) s_d[p] = sv[s];
+                        if (p < D) s_df[p] = make_float4(sh[s].x, sh[s].y, sl[s].x, sl[s].y);
                     }
                     __syncwarp();
-                    double2 rv[NS];
-                    double rmax = 0.0;
+                    float rr[NS][2];
+                    float rmax = 0.f;
 #pragma unroll
                     for (int s = 0; s < NS; ++s) {
                         const int p = lane + 32 * s;
-                        double2 acc = make_double2(0.0, 0.0);
+                        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
                         if (p < D) {
-                            const double2 yp = to_d2(K[NPK + p]);
-                            acc.x = yp.x - lambda * sv[s].x;
-                            acc.y = yp.y - lambda * sv[s].y;
+                            const V yp = K[NPK + p];
+                            acc = make_float4(yp.x, 0.f, yp.y, 0.f);
+                            df_sub_cmul(acc, make_float2(lamf, 0.f), sh[s], sl[s]);
                             for (int q = 0; q <= p; ++q) {   // K_pq s_q
-                                const double2 kk = Kd[tri(p, q)], sq = s_d[q];
-                                acc.x -= kk.x * sq.x - kk.y * sq.y;
-                                acc.y -= kk.x * sq.y + kk.y * sq.x;
+                                const float4 sq = s_df[q];
+                                df_sub_cmul(acc, K[tri(p, q)], make_float2(sq.x, sq.y), make_float2(sq.z, sq.w));
                             }
                             for (int q = p + 1; q < D; ++q) {  // conj(K_qp) s_q
-                                const double2 kk = Kd[tri(q, p)], sq = s_d[q];
-                                acc.x -= kk.x * sq.x + kk.y * sq.y;
-                                acc.y -= kk.x * sq.y - kk.y * sq.x;
+                                const float4 sq = s_df[q];
+                                const V kq = K[tri(q, p)];
+                                df_sub_cmul(acc, make_float2(kq.x, -kq.y), make_float2(sq.x, sq.y),
+                                            make_float2(sq.z, sq.w));
                             }
                         }
-                        rv[s] = acc;
-                        rmax = fmax(rmax, fmax(fabs(acc.x), fabs(acc.y)));
+                        rr[s][0] = acc.x + acc.y;
+                        rr[s][1] = acc.z + acc.w;
+                        rmax = fmaxf(rmax, fmaxf(fabsf(rr[s][0]), fabsf(rr[s][1])));
                     }
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-                    const double sc = rmax > 0.0 ? rmax : 1.0;
-                    const double isc = 1.0 / sc;
+                    for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+                    const float sc = rmax > 0.f ? rmax : 1.f;
+                    const float isc = 1.f / sc;
 #pragma unroll
                     for (int s = 0; s < NS; ++s) {
-                        bv[s] = from_d2<V>(make_double2(rv[s].x * isc, rv[s].y * isc));
-                        bv[s].x *= scl[s];
-                        bv[s].y *= scl[s];
+                        bv[s].x = rr[s][0] * isc * scl[s];
+                        bv[s].y = rr[s][1] * isc * scl[s];
                     }
                     warp_chol_solve<V, T, NS>(Lm, D, bv, lane);
-                    dmax = 0.0;
-                    smax = 0.0;
+                    dmax = 0.f;
+                    smax = 0.f;
 #pragma unroll
                     for (int s = 0; s < NS; ++s) {
-                        const double dx = (double)(bv[s].x * scl[s]) * sc, dy = (double)(bv[s].y * scl[s]) * sc;
-                        sv[s].x += dx;
-                        sv[s].y += dy;
-                        dmax = fmax(dmax, fmax(fabs(dx), fabs(dy)));
-                        smax = fmax(smax, fmax(fabs(sv[s].x), fabs(sv[s].y)));
+                        const float dx = bv[s].x * scl[s] * sc, dy = bv[s].y * scl[s] * sc;
+                        float t, e;
+                        two_sum(sh[s].x, dx, t, e); sh[s].x = t; sl[s].x += e;
+                        two_sum(sh[s].y, dy, t, e); sh[s].y = t; sl[s].y += e;
+                        dmax = fmaxf(dmax, fmaxf(fabsf(dx), fabsf(dy)));
+                        smax = fmaxf(smax, fmaxf(fabsf(sh[s].x), fabsf(sh[s].y)));
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
-                        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-                        smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+                        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+                        smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
                     }
-                    if (dmax <= 1e-6 * smax) break;
+                    if (lane == 0) atomicAdd(nsteps, 1ull);
+                    // after a step with relative correction rho the remaining error is
+                    // about rho^2: stop once that is below 1e-10
+                    if (dmax <= 1e-5f * smax) break;
                 }
+#pragma unroll
+                for (int s = 0; s < NS; ++s)
+                    sv[s] = make_double2((double)sh[s].x + (double)sl[s].x, (double)sh[s].y + (double)sl[s].y);
                 conv = dmax <= 1e-4 * smax;
             }
             ok = conv;
             if (!conv) {
-                // FP64 Cholesky of the same system in the slice's FP64 record
-                double2* Kd = fb + (size_t)k * NPK;
-                __syncwarp();
-                for (int q = lane; q < NPK; q += 32) Kd[q] = to_d2(K[q]);
-                __syncwarp();
-                for (int p = lane; p < D; p += 32) Kd[tri(p, p)].x += lambda;
-                ok = warp_chol<double2, double>(Kd, D, tol, lane);
-                if (ok) {
-#pragma unroll
-                    for (int s = 0; s < NS; ++s) {
-                        const int p = lane + 32 * s;
-                        sv[s] = p < D ? to_d2(K[NPK + p]) : make_double2(0.0, 0.0);
-                    }
-                    warp_chol_solve<double2, double, NS>(Kd, D, sv, lane);
-                }
-                if (lane == 0) atomicAdd(nref, 1ull);
+                // solved afterwards in FP64 by k_mid_fallback (slice and its entries untouched here)
+                if (lane == 0) fblist[atomicAdd(nfb, 1ull)] = k;
+                continue;
             }
         } else {
-            ok = warp_chol<V, T>(Lm, D, (T)tol, lane);
+            ok = warp_chol<V, T, NS>(Lm, D, (T)tol, lane);
             if (ok) {
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
@@ -882,20 +1044,73 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
         }
         __syncwarp();
         // left environment update into the next order
-        const int s0 = seg[k], s1 = seg[k + 1];
-        for (int p = s0 + lane; p < s1; p += 32) {
-            V h[R];
+        slice_h_update<T, R>(H, zt_s, nxt, Hn, seg[k], seg[k + 1], lane);
+    }
+}
+
+// FP64 fallback of the precision form: one warp per slice listed by
+// k_mid_solve (complex64 factorization broke down or refinement did not
+// contract): FP64 Cholesky of K + lambda I in the slice's FP64 record, solve,
+// slice write (or keep the old slice and count it singular), left update.
+template <typename T, int R>
+__global__ void __launch_bounds__(32 * SolveCfg<T, R>::WPB)
+k_mid_fallback(const typename cvec<T>::type* __restrict__ rec, const typename cvec<T>::type* __restrict__ H,
+               const int32_t* __restrict__ seg, const int32_t* __restrict__ nxt,
+               typename cvec<T>::type* __restrict__ Hn, double2* __restrict__ Zd,
+               typename cvec<T>::type* __restrict__ Zt, double2* __restrict__ fb, double lambda_in, double ridge,
+               unsigned long long* __restrict__ nsing, const unsigned long long* __restrict__ nfb,
+               const int32_t* __restrict__ fblist)
+{
+    typedef typename cvec<T>::type V;
+    typedef SolveCfg<T, R> C;
+    constexpr int D = C::D, NPK = C::NPK, NS = C::NS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    V* zt_s = (V*)(smem + (size_t)wib * C::WBYTES);
+    const long long count = (long long)*nfb;
+    for (long long idx = (long long)blockIdx.x * C::WPB + wib; idx < count; idx += (long long)gridDim.x * C::WPB) {
+        const int k = fblist[idx];
+        const V* K = rec + (size_t)k * (NPK + D);
+        double tr = 0.0;
+        for (int p = lane; p < D; p += 32) tr += (double)K[tri(p, p)].x;
 #pragma unroll
-            for (int a = 0; a < R; ++a) h[a] = H[(size_t)p * R + a];
-            const size_t o = (size_t)nxt[p] * R;
+        for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        const double lambda = fmax(lambda_in, ridge * tr / D);
+        const double tol = lambda > 0.0 ? 0.0 : 1e-14 * (tr + D * lambda);
+        double2* Kd = fb + (size_t)k * NPK;
+        __syncwarp();
+        for (int q = lane; q < NPK; q += 32) Kd[q] = to_d2(K[q]);
+        __syncwarp();
+        for (int p = lane; p < D; p += 32) Kd[tri(p, p)].x += lambda;
+        double2 sv[NS];
+        const bool ok = warp_chol<double2, double, NS>(Kd, D, tol, lane);
+        if (ok) {
 #pragma unroll
-            for (int c = 0; c < R; ++c) {
-                V acc2 = czero<V>();
+            for (int s = 0; s < NS; ++s) {
+                const int p = lane + 32 * s;
+                sv[s] = p < D ? to_d2(K[NPK + p]) : make_double2(0.0, 0.0);
+            }
+            warp_chol_solve<double2, double, NS>(Kd, D, sv, lane);
+        } else if (lane == 0) {
+            atomicAdd(nsing, 1ull);
+        }
+        __syncwarp();
 #pragma unroll
-                for (int a = 0; a < R; ++a) cmac(acc2, h[a], zt_s[a * R + c]);
-                Hn[o + c] = acc2;
+        for (int s = 0; s < NS; ++s) {
+            const int p = lane + 32 * s;
+            if (p < D) {
+                if (ok) {
+                    Zd[(size_t)k * D + p] = sv[s];
+                    const V st = from_d2<V>(sv[s]);
+                    Zt[(size_t)k * D + p] = st;
+                    zt_s[p] = st;
+                } else {
+                    zt_s[p] = Zt[(size_t)k * D + p];
+                }
             }
         }
+        __syncwarp();
+        slice_h_update<T, R>(H, zt_s, nxt, Hn, seg[k], seg[k + 1], lane);
     }
 }
 

@@ -20,6 +20,9 @@ template <typename T, int R> struct Path {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_mid_solve<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SolveCfg<T, R>::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_mid_fallback<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SolveCfg<T, R>::SMEM);
         if (e != cudaSuccess)
             return fail(c, BFC_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
         return BFC_OK;
@@ -109,10 +112,19 @@ template <typename T, int R> struct Path {
             }
             {
                 ProfScope ps(c, "mid_solve");
+                if (SC::MIXED) cudaMemsetAsync(c->d_count + 3, 0, sizeof(unsigned long long), c->stream);
                 k_mid_solve<T, R><<<gsolve, 32 * SC::WPB, SC::SMEM, c->stream>>>(
                     (const V*)c->rec, hin, c->seg[m], c->nxt[m], hout, c->Zd + (size_t)(m - 1) * S * R * R,
                     (V*)c->Zt + (size_t)(m - 1) * S * R * R, c->fb, c->P.lambda, c->ridge, c->d_count,
-                    c->d_count + 1, (int)S);
+                    c->d_count + 3, c->d_count + 2, c->fblist, (int)S);
+            }
+            if (SC::MIXED) {
+                ProfScope ps(c, "mid_fallback");
+                k_mid_fallback<T, R><<<gsolve, 32 * SC::WPB, SC::SMEM, c->stream>>>(
+                    (const V*)c->rec, hin, c->seg[m], c->nxt[m], hout, c->Zd + (size_t)(m - 1) * S * R * R,
+                    (V*)c->Zt + (size_t)(m - 1) * S * R * R, c->fb, c->P.lambda, c->ridge, c->d_count,
+                    c->d_count + 3, c->fblist);
+                launch_add_u64(c->d_count + 1, c->d_count + 3, c->stream);  // fallbacks of the sweep
             }
         }
         BFC_LAUNCH_CHECK(c, "middle levels");

@@ -287,6 +287,12 @@ __global__ void k_embed(const double2* __restrict__ A, const double2* __restrict
     }
 }
 
+// *dst += *src for device counters
+__global__ void k_add_u64(unsigned long long* __restrict__ dst, const unsigned long long* __restrict__ src)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst += *src;
+}
+
 // ------------------------------------------------------------ launchers
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -318,6 +324,10 @@ void launch_all_keys(const int32_t* ii, const int32_t* jj, int64_t M, int L, int
                      cudaStream_t st)
 {
     k_all_keys<<<nblk(M, 256), 256, 0, st>>>(ii, jj, M, L, b, keys);
+}
+void launch_add_u64(unsigned long long* dst, const unsigned long long* src, cudaStream_t st)
+{
+    k_add_u64<<<1, 32, 0, st>>>(dst, src);
 }
 void launch_invert(const int32_t* perm, int64_t N, int32_t* pos, cudaStream_t st)
 {

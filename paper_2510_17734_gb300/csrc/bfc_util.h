@@ -23,6 +23,7 @@ cudaError_t sort_level(const int32_t* d_i, const int32_t* d_j, int64_t N, int le
 
 void launch_all_keys(const int32_t* ii, const int32_t* jj, int64_t M, int L, int b, int32_t* keys,
                      cudaStream_t st);
+void launch_add_u64(unsigned long long* dst, const unsigned long long* src, cudaStream_t st);
 void launch_invert(const int32_t* perm, int64_t N, int32_t* pos, cudaStream_t st);
 void launch_compose(const int32_t* perm, const int32_t* pos_other, int64_t N, int32_t* out, cudaStream_t st);
 void launch_gather_i32(const int32_t* src, const int32_t* perm, int64_t N, int32_t* out, cudaStream_t st);
