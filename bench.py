@@ -241,7 +241,10 @@ def run_bfc(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    prob = synth.config(3)
+    prob = synth.config(3, n_override=args.n or None)
+    workload = WORKLOAD if not args.n else (
+        f"n={prob.n} L={prob.L} b={prob.b} r={prob.r}, the n=65536 construction at reduced n "
+        f"(profiling case, {prob.nnz} train entries)")
     prec = bfc.PREC_C64 if args.prec == "c64" else bfc.PREC_FP64
 
     c = lowrank_start(prob, bfc, prec)
@@ -298,7 +301,7 @@ def run_bfc(args, rank, world, local_rank):
     e2e_value = world * prob.nnz / (e2e_ms * 1e-3)
 
     # roofline of the dominant kernel (per-slice normal equations + solve)
-    launches = sum(v[0] for v in prof.values())
+    launches = sum(int(st["launches"]) for st in stats)   # kernels launched by the timed sweeps
     mid_n, mid_ms = prof.get("mid_gram", (0, 0.0))
     if mid_n == 0 or mid_ms <= 0.0:
         raise RuntimeError(f"no timing for the normal-equation kernel in the profile: {sorted(prof)}")
@@ -318,7 +321,7 @@ def run_bfc(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64+f64" if prec == bfc.PREC_C64 else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.prec,
+            "config": {"workload": workload, "precision": args.prec,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "working set > L2 (no flush)", "nnz_train": prob.nnz},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * P,
@@ -369,6 +372,8 @@ def main():
     ap.add_argument("--prec", default="c64", choices=["c64", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance runs")
+    ap.add_argument("--n", type=int, default=0,
+                    help="reduced n with the same construction (small profiling captures only)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

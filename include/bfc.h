@@ -109,7 +109,8 @@ typedef struct {
     double entries_per_s;   /* training entries / sweep time                 */
     int64_t singular_slices;/* systems left unchanged (Cholesky breakdown)   */
     int64_t refined_fallbacks; /* precision form: FP64 Cholesky fallbacks    */
-    int64_t refine_steps;   /* precision form: FP64 refinement steps taken   */
+    int64_t refine_steps;   /* precision form: refinement steps taken        */
+    int64_t launches;       /* kernels this call launched (sweep + errors)   */
 } bfc_sweep_stats;
 
 typedef struct {
@@ -170,6 +171,19 @@ bfc_status bfc_als_sweep(bfc_ctx* ctx, bfc_sweep_stats* out);
  * regularization term, matching include_reg). */
 bfc_status bfc_grad(bfc_ctx* ctx, int32_t include_reg, double* grad_packed,
                     double* objective);
+
+/* Gradient completion: `iters` iterations of limited-memory BFGS on the 2P
+ * real parameters (the packed factors viewed as doubles) of the regularized
+ * objective f, with the gradients of bfc_grad (Eqs. (grad_butterfly_*)).
+ * Two-loop recursion with `memory` pairs (1..64) and H0 = gamma I (gamma =
+ * s^T y / y^T y of the newest pair); backtracking Armijo line search
+ * (c1 = 1e-4, step halved, at most 30 trials) starting from step 1, or from
+ * 1 / ||g|| before the first pair; a pair is kept only if
+ * s^T y > 1e-12 ||s|| ||y||.  The factors end at the last accepted point.
+ * history (may be NULL) receives per-iteration training / test errors and f;
+ * *done (may be NULL) the iterations run. */
+bfc_status bfc_lbfgs(bfc_ctx* ctx, int32_t iters, int32_t memory, bfc_sweep_stats* history,
+                     int32_t history_cap, int32_t* done);
 
 /* Low-rank start (Sec. 4.2): low-rank matrix completion of rank R <= r from
  * the caller's starting factors A0, B0 (n x R packed complex128, X = A B^T),

@@ -19,6 +19,8 @@ Functions and the passage each follows:
   embed_lowrank            identity embedding of A B^T (stand-in for Alg. 2)
   lr_complete              Alg. 1 with L = 0 (low-rank matrix completion,
                            Sec. 4.2)
+  lbfgs                    gradient completion of f by limited-memory BFGS
+                           (Nocedal and Wright, Alg. 7.4) over grad()
 """
 from __future__ import annotations
 
@@ -184,3 +186,53 @@ def lr_complete(n, R, lam, A0, B0, i, j, t, sweeps):
     for _ in range(sweeps):
         packed, _st = als_sweep(n, 0, n, R, lam, packed, i, j, t)
     return packed[:n * R].reshape(n, R), packed[n * R:].reshape(n, R)
+
+
+def lbfgs(n, L, b, r, lam, packed, i, j, t, iters, memory=10, c1=1e-4):
+    """Limited-memory BFGS on the 2P real parameters (Re, Im interleaved) of
+    f = 1/2 sum |x - t|^2 + lambda/2 ||S||^2, gradients from grad().
+    Two-loop recursion, H0 = gamma I with gamma = s^T y / y^T y of the newest
+    pair; backtracking Armijo line search (c1, halving, <= 30 trials) from
+    step 1, or 1/||g|| before the first pair; a pair is kept only if
+    s^T y > 1e-12 ||s|| ||y||.  Returns (final packed factors, objectives)."""
+    def fg(xr):
+        g, f = grad(n, L, b, r, lam, xr.view(np.complex128), i, j, t, include_reg=True)
+        return f, g.view(np.float64).copy()
+
+    x = _c128(packed).copy().view(np.float64)
+    f, g = fg(x)
+    S, Y, rho, hist = [], [], [], []
+    for k in range(iters):
+        q = g.copy()
+        alpha = [0.0] * len(S)
+        for idx in range(len(S) - 1, -1, -1):
+            alpha[idx] = rho[idx] * float(S[idx] @ q)
+            q -= alpha[idx] * Y[idx]
+        gamma = float(S[-1] @ Y[-1]) / float(Y[-1] @ Y[-1]) if S else 1.0
+        d = gamma * q
+        for idx in range(len(S)):
+            beta = rho[idx] * float(Y[idx] @ d)
+            d += S[idx] * (alpha[idx] - beta)
+        d = -d
+        gtd = float(g @ d)
+        if not gtd < 0.0:
+            d = -g
+            gtd = -float(g @ g)
+        step = 1.0 / float(np.sqrt(g @ g)) if (not S and k == 0) else 1.0
+        for _ in range(30):
+            xt = x + step * d
+            ft, gt = fg(xt)
+            if ft <= f + c1 * step * gtd:
+                break
+            step *= 0.5
+        s_, y_ = xt - x, gt - g
+        sy = float(s_ @ y_)
+        if sy > 1e-12 * float(np.linalg.norm(s_)) * float(np.linalg.norm(y_)):
+            S.append(s_)
+            Y.append(y_)
+            rho.append(1.0 / sy)
+            if len(S) > memory:
+                S.pop(0), Y.pop(0), rho.pop(0)
+        x, g, f = xt, gt, ft
+        hist.append(f)
+    return x.view(np.complex128).copy(), hist

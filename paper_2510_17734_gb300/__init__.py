@@ -25,7 +25,7 @@ __all__ = [
     "bfc_num_params", "bfc_create", "bfc_set_stream", "bfc_set_factors", "bfc_get_factors",
     "bfc_eval", "bfc_als_sweep", "bfc_grad", "bfc_lowrank_init", "bfc_complete",
     "bfc_profile_enable", "bfc_profile_read", "bfc_last_error", "bfc_destroy",
-    "bfc_decode", "bfc_get_order", "bfc_residual_noalloc",
+    "bfc_decode", "bfc_get_order", "bfc_residual_noalloc", "bfc_lbfgs",
 ]
 
 PREC_FP64 = 0
@@ -36,7 +36,7 @@ STATUS = {0: "BFC_OK", 1: "BFC_EINVAL", 2: "BFC_ENOMEM", 3: "BFC_ECUDA", 4: "BFC
 # Every entry point declared in include/bfc.h.
 exported_symbols = (
     "bfc_num_params", "bfc_create", "bfc_set_stream", "bfc_set_factors", "bfc_get_factors",
-    "bfc_eval", "bfc_als_sweep", "bfc_grad", "bfc_lowrank_init", "bfc_complete",
+    "bfc_eval", "bfc_als_sweep", "bfc_grad", "bfc_lbfgs", "bfc_lowrank_init", "bfc_complete",
     "bfc_decode", "bfc_get_order", "bfc_residual_noalloc",
     "bfc_profile_enable", "bfc_profile_read", "bfc_last_error", "bfc_destroy",
 )
@@ -62,7 +62,7 @@ class SweepStats(ctypes.Structure):
                 ("test_rel_err", ctypes.c_double), ("objective", ctypes.c_double),
                 ("sweep_ms", ctypes.c_double), ("entries_per_s", ctypes.c_double),
                 ("singular_slices", ctypes.c_int64), ("refined_fallbacks", ctypes.c_int64),
-                ("refine_steps", ctypes.c_int64)]
+                ("refine_steps", ctypes.c_int64), ("launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -111,6 +111,8 @@ def load():
         lib.bfc_als_sweep.restype = i32
         lib.bfc_grad.argtypes = [vp, i32, vp, ctypes.POINTER(dbl)]
         lib.bfc_grad.restype = i32
+        lib.bfc_lbfgs.argtypes = [vp, i32, i32, sp, i32, ctypes.POINTER(i32)]
+        lib.bfc_lbfgs.restype = i32
         lib.bfc_lowrank_init.argtypes = [vp, i32, i32, vp, vp]
         lib.bfc_lowrank_init.restype = i32
         lib.bfc_complete.argtypes = [vp, sp, i32, ctypes.POINTER(i32)]
@@ -208,6 +210,13 @@ def bfc_grad(ctx, include_reg: bool, grad_out=None) -> float:
     return float(obj.value)
 
 
+def bfc_lbfgs(ctx, iters: int, memory: int = 10):
+    hist = (SweepStats * max(iters, 1))()
+    done = ctypes.c_int32(0)
+    _check(load().bfc_lbfgs(ctx, iters, memory, hist, iters, ctypes.byref(done)), ctx)
+    return [hist[q] for q in range(done.value)]
+
+
 def bfc_lowrank_init(ctx, R: int, sweeps: int, A0, B0):
     _check(load().bfc_lowrank_init(ctx, R, sweeps, _ptr(A0), _ptr(B0)), ctx)
 
@@ -301,6 +310,9 @@ class Completion:
         g = np.zeros(self.P, dtype=np.complex128)
         f = bfc_grad(self.ctx, include_reg, g)
         return g, f
+
+    def lbfgs(self, iters, memory=10):
+        return [h.as_dict() for h in bfc_lbfgs(self.ctx, iters, memory)]
 
     def lowrank_init(self, A0, B0, sweeps):
         A0, B0 = _host_c128(A0), _host_c128(B0)

@@ -60,8 +60,9 @@ bfc_status ensure_tmp(Ctx* c, size_t bytes)
     return BFC_OK;
 }
 
-ProfScope::ProfScope(Ctx* ctx, const char* name) : c(ctx)
+ProfScope::ProfScope(Ctx* ctx, const char* name, int k) : c(ctx), kernels(k)
 {
+    c->n_launch += k;
     if (!c->prof) return;
     for (size_t q = 0; q < c->prof_rec.size(); ++q)
         if (c->prof_rec[q].name == name) { rec = (int)q; break; }
@@ -90,7 +91,7 @@ ProfScope::~ProfScope()
         c->ev_pool.pop_back();
     }
     cudaEventRecord(b, c->stream);
-    c->prof_pending.push_back(ProfPending{rec, a, b});
+    c->prof_pending.push_back(ProfPending{rec, kernels, a, b});
 }
 
 void prof_collect(Ctx* c)
@@ -100,7 +101,7 @@ void prof_collect(Ctx* c)
     for (auto& p : c->prof_pending) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-            c->prof_rec[p.rec].launches += 1;
+            c->prof_rec[p.rec].launches += p.kernels;
             c->prof_rec[p.rec].total_ms += ms;
         }
         c->ev_pool.push_back(p.a);
@@ -377,6 +378,7 @@ static bfc_status test_error(Ctx* c, int slot)
 static bfc_status sweep_impl(Ctx* c, bfc_sweep_stats* out)
 {
     const Ops* ops = get_ops(c->fp32, c->r);
+    const int64_t launched0 = c->n_launch;
     BFC_CK(c, cudaMemsetAsync(c->d_count, 0, 3 * sizeof(unsigned long long), c->stream));
     BFC_CK(c, cudaEventRecord(c->ev0, c->stream));
     BFC_TRY(ops->sweep(c));
@@ -387,7 +389,181 @@ static bfc_status sweep_impl(Ctx* c, bfc_sweep_stats* out)
     BFC_TRY(sync(c));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-    return collect_stats(c, out, ms);
+    BFC_TRY(collect_stats(c, out, ms));
+    if (out) out->launches = c->n_launch - launched0;
+    return BFC_OK;
+}
+
+
+// Gradient of f (with lambda S when include_reg) into the device vector G;
+// hs[0] = sum |x - t|^2 over the training entries, hs[2] = ||S||^2.
+static bfc_status grad_into(Ctx* c, int include_reg, double2* G, double* hs)
+{
+    double* part = c->d_red;  // per-fiber partial fits
+    const Ops* ops = get_ops(c->fp32, c->r);
+    BFC_TRY(ops->grad(c, G, part));
+    {
+        ProfScope ps(c, "reduce");
+        launch_reduce_single(part, c->n, c->d_scalars + 0, c->stream);
+    }
+    BFC_TRY(factor_sumsq(c, 2));
+    if (include_reg) launch_axpy((double*)G, (const double*)c->z1d, c->P.lambda, 2 * c->Pn, c->stream);
+    BFC_LAUNCH_CHECK(c, "grad tail");
+    BFC_CK(c, cudaMemcpyAsync(hs, c->d_scalars, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+// Dot product of two device vectors of n doubles, returned on the host.
+static bfc_status ddot(Ctx* c, const double* a, const double* b, int64_t n, double* out)
+{
+    const int nb = (int)std::min<int64_t>(1216, (n + 255) / 256);
+    launch_dot(a, b, n, c->d_red, nb, c->d_scalars + 8, c->stream);
+    BFC_LAUNCH_CHECK(c, "dot");
+    BFC_CK(c, cudaMemcpyAsync(out, c->d_scalars + 8, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+// Limited-memory BFGS on the 2P real parameters (the packed factors viewed as
+// doubles) of the regularized objective f (Eq. BF_objective + lambda/2 ||S||^2),
+// with gradients from the gradient sweep (Eqs. grad_butterfly_*).  Two-loop
+// recursion (Nocedal and Wright, Alg. 7.4) with memory m and H0 = gamma I,
+// gamma = s^T y / y^T y of the newest pair; backtracking Armijo line search
+// (c1 = 1e-4, halving, at most 30 trials) from step 1, or 1 / ||g|| before
+// the first pair exists; a pair is stored only if s^T y > 1e-12 ||s|| ||y||.
+// The vector algebra runs on the device; only scalars come back.
+static bfc_status lbfgs_impl(Ctx* c, int iters, int m, bfc_sweep_stats* history, int cap, int32_t* done)
+{
+    const int64_t M = 2 * c->Pn;  // doubles
+    const size_t vb = (size_t)M * sizeof(double);
+    std::vector<double*> S(m, nullptr), Y(m, nullptr);
+    double *x = nullptr, *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr;
+    std::vector<void*> bufs;
+    auto get = [&](double** p) -> bfc_status {
+        BFC_TRY(dalloc(c, (void**)p, vb, "L-BFGS vectors"));
+        bufs.push_back(*p);
+        return BFC_OK;
+    };
+    bfc_status st = BFC_OK;
+    for (auto** p : {&x, &g, &d, &xt, &gt})
+        if (st == BFC_OK) st = get(p);
+    for (int q = 0; q < m && st == BFC_OK; ++q) {
+        st = get(&S[q]);
+        if (st == BFC_OK) st = get(&Y[q]);
+    }
+    auto release = [&]() {
+        cudaStreamSynchronize(c->stream);
+        for (void* p : bufs) dfree(c, p);
+    };
+    if (st != BFC_OK) { release(); return st; }
+    std::vector<double> rho(m, 0.0), alpha(m, 0.0);
+    int npairs = 0, head = 0;  // ring buffer of pairs: newest at (head - 1) mod m
+    double hs[3];
+    const double lam = c->P.lambda;
+    auto objective = [&](const double* h) { return 0.5 * h[0] + 0.5 * lam * h[2]; };
+    // training-value norm for the relative error
+    double tnorm2 = 0.0;
+    launch_sumsq(c->d_t, c->N, c->d_red, 1, c->stream);
+    st = cudaMemcpyAsync(&tnorm2, c->d_red, sizeof(double), cudaMemcpyDeviceToHost, c->stream) == cudaSuccess
+             ? sync(c) : fail(c, BFC_ECUDA, "copy");
+    if (st == BFC_OK) st = cudaMemcpyAsync(x, c->z1d, vb, cudaMemcpyDeviceToDevice, c->stream) == cudaSuccess
+                               ? BFC_OK : fail(c, BFC_ECUDA, "copy");
+    if (st == BFC_OK) st = grad_into(c, 1, (double2*)g, hs);
+    double f = objective(hs);
+    int k = 0;
+    for (; k < iters && st == BFC_OK; ++k) {
+        BFC_CK(c, cudaEventRecord(c->ev0, c->stream));
+        // two-loop recursion: d = -H g
+        BFC_CK(c, cudaMemcpyAsync(d, g, vb, cudaMemcpyDeviceToDevice, c->stream));
+        for (int q = 0; q < npairs && st == BFC_OK; ++q) {
+            const int idx = ((head - 1 - q) % m + m) % m;
+            double sq;
+            st = ddot(c, S[idx], d, M, &sq);
+            alpha[idx] = rho[idx] * sq;
+            launch_axpy(d, Y[idx], -alpha[idx], M, c->stream);
+        }
+        double gamma = 1.0;
+        if (npairs > 0 && st == BFC_OK) {
+            const int idx = ((head - 1) % m + m) % m;
+            double yy;
+            st = ddot(c, Y[idx], Y[idx], M, &yy);
+            gamma = 1.0 / (rho[idx] * yy);
+        }
+        launch_axpby(d, gamma, d, 0.0, d, M, c->stream);
+        for (int q = npairs - 1; q >= 0 && st == BFC_OK; --q) {
+            const int idx = ((head - 1 - q) % m + m) % m;
+            double yr;
+            st = ddot(c, Y[idx], d, M, &yr);
+            launch_axpy(d, S[idx], alpha[idx] - rho[idx] * yr, M, c->stream);
+        }
+        launch_axpby(d, -1.0, d, 0.0, d, M, c->stream);
+        double gtd = 0.0, gg = 0.0;
+        if (st == BFC_OK) st = ddot(c, g, d, M, &gtd);
+        if (st == BFC_OK) st = ddot(c, g, g, M, &gg);
+        if (st != BFC_OK) break;
+        if (!(gtd < 0.0)) {  // not a descent direction: fall back to steepest descent
+            launch_axpby(d, -1.0, g, 0.0, g, M, c->stream);
+            gtd = -gg;
+        }
+        double step = (npairs == 0 && k == 0) ? 1.0 / std::sqrt(gg) : 1.0;
+        double ft = f;
+        for (int ls = 0; ls < 30 && st == BFC_OK; ++ls) {
+            launch_axpby(xt, 1.0, x, step, d, M, c->stream);
+            BFC_CK(c, cudaMemcpyAsync(c->z1d, xt, vb, cudaMemcpyDeviceToDevice, c->stream));
+            st = refresh_copies(c);
+            if (st == BFC_OK) st = grad_into(c, 1, (double2*)gt, hs);
+            ft = objective(hs);
+            if (ft <= f + 1e-4 * step * gtd) break;
+            step *= 0.5;
+        }
+        if (st != BFC_OK) break;
+        // new pair s = xt - x, y = gt - g
+        const int slot = head;
+        launch_axpby(S[slot], 1.0, xt, -1.0, x, M, c->stream);
+        launch_axpby(Y[slot], 1.0, gt, -1.0, g, M, c->stream);
+        double sy = 0.0, ss = 0.0, yy = 0.0;
+        st = ddot(c, S[slot], Y[slot], M, &sy);
+        if (st == BFC_OK) st = ddot(c, S[slot], S[slot], M, &ss);
+        if (st == BFC_OK) st = ddot(c, Y[slot], Y[slot], M, &yy);
+        if (st != BFC_OK) break;
+        if (sy > 1e-12 * std::sqrt(ss) * std::sqrt(yy)) {
+            rho[slot] = 1.0 / sy;
+            head = (head + 1) % m;
+            npairs = std::min(npairs + 1, m);
+        }
+        std::swap(x, xt);
+        std::swap(g, gt);
+        f = ft;
+        if (c->NT > 0) {
+            st = test_error(c, 3);
+            if (st == BFC_OK) st = sync(c);
+        }
+        BFC_CK(c, cudaEventRecord(c->ev1, c->stream));
+        double th[2] = {0.0, 1.0};
+        if (c->NT > 0) BFC_CK(c, cudaMemcpyAsync(th, c->d_scalars + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (st == BFC_OK) st = sync(c);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        if (history && k < cap) {
+            bfc_sweep_stats& h = history[k];
+            memset(&h, 0, sizeof(h));
+            h.sweep = k + 1;
+            h.train_rel_err = tnorm2 > 0 ? std::sqrt(hs[0] / tnorm2) : std::sqrt(hs[0]);
+            h.test_rel_err = c->NT > 0 ? (th[1] > 0 ? std::sqrt(th[0] / th[1]) : std::sqrt(th[0])) : -1.0;
+            h.objective = f;
+            h.sweep_ms = ms;
+            h.entries_per_s = ms > 0 ? (double)c->N / (ms * 1e-3) : 0.0;
+        }
+    }
+    if (done) *done = k;
+    // the factors hold the last evaluated point; make them the accepted one
+    if (st == BFC_OK) {
+        if (cudaMemcpyAsync(c->z1d, x, vb, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            st = fail(c, BFC_ECUDA, "copy");
+        if (st == BFC_OK) st = refresh_copies(c);
+    }
+    release();
+    if (st == BFC_OK) st = sync(c);
+    return st;
 }
 
 }  // namespace bfc
@@ -479,19 +655,24 @@ bfc_status bfc_grad(bfc_ctx* ctx, int32_t include_reg, double* grad_packed, doub
     const size_t gb = (size_t)c->Pn * 16;
     BFC_TRY(ensure_tmp(c, gb + 256));
     double2* G = (double2*)c->d_tmp;
-    double* part = c->d_red;  // n fiber partials
-    const Ops* ops = get_ops(c->fp32, c->r);
-    BFC_TRY(ops->grad(c, G, part));
-    launch_reduce_single(part, c->n, c->d_scalars + 0, c->stream);
-    BFC_TRY(factor_sumsq(c, 2));
-    if (include_reg) launch_axpy((double*)G, (const double*)c->z1d, c->P.lambda, 2 * c->Pn, c->stream);
-    BFC_LAUNCH_CHECK(c, "grad tail");
     double hs[3];
-    BFC_CK(c, cudaMemcpyAsync(hs, c->d_scalars, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    if (grad_packed) BFC_CK(c, cudaMemcpyAsync(grad_packed, G, gb, out_kind(c), c->stream));
-    BFC_TRY(sync(c));
+    BFC_TRY(grad_into(c, include_reg, G, hs));
+    if (grad_packed) {
+        BFC_CK(c, cudaMemcpyAsync(grad_packed, G, gb, out_kind(c), c->stream));
+        BFC_TRY(sync(c));
+    }
     if (objective) *objective = 0.5 * hs[0] + (include_reg ? 0.5 * c->P.lambda * hs[2] : 0.0);
     return BFC_OK;
+}
+
+bfc_status bfc_lbfgs(bfc_ctx* ctx, int32_t iters, int32_t memory, bfc_sweep_stats* history, int32_t history_cap,
+                     int32_t* done)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    if (done) *done = 0;
+    if (iters < 0 || memory < 1 || memory > 64) return fail(c, BFC_EINVAL, "iters >= 0 and 1 <= memory <= 64 required");
+    return lbfgs_impl(c, iters, memory, history, history_cap, done);
 }
 
 bfc_status bfc_lowrank_init(bfc_ctx* ctx, int32_t R, int32_t sweeps, const double* A0, const double* B0)

@@ -20,6 +20,7 @@ struct ProfRecord {
 };
 struct ProfPending {
     int rec;
+    int kernels;
     cudaEvent_t a, b;
 };
 
@@ -82,6 +83,7 @@ struct Ctx {
 
     // profiling
     bool prof = false;
+    int64_t n_launch = 0;           // kernels launched by this context so far
     std::vector<ProfRecord> prof_rec;
     std::vector<ProfPending> prof_pending;
     std::vector<cudaEvent_t> ev_pool;
@@ -97,8 +99,11 @@ bfc_status ensure_tmp(Ctx* c, size_t bytes);
 struct ProfScope {
     Ctx* c;
     int rec = -1;
+    int kernels = 1;
     cudaEvent_t a = nullptr;
-    ProfScope(Ctx* ctx, const char* name);
+    // `kernels`: how many kernels the scope launches (added to Ctx::n_launch
+    // whether or not profiling is on).
+    ProfScope(Ctx* ctx, const char* name, int kernels = 1);
     ~ProfScope();
 };
 void prof_collect(Ctx* c);

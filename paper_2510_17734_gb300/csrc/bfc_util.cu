@@ -287,6 +287,32 @@ __global__ void k_embed(const double2* __restrict__ A, const double2* __restrict
     }
 }
 
+// Per-block partial dot products of two double vectors (deterministic order).
+__global__ void __launch_bounds__(256) k_dot(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                                             double* __restrict__ part)
+{
+    __shared__ double sw[8];
+    double s = 0.0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        s += a[q] * b[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sw[q];
+        part[blockIdx.x] = t;
+    }
+}
+
+// y = a x + b z
+__global__ void k_axpby(double* __restrict__ y, double a, const double* __restrict__ x, double b,
+                        const double* __restrict__ z, int64_t n)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) y[q] = a * x[q] + b * z[q];
+}
+
 // *dst += *src for device counters
 __global__ void k_add_u64(unsigned long long* __restrict__ dst, const unsigned long long* __restrict__ src)
 {
@@ -324,6 +350,16 @@ void launch_all_keys(const int32_t* ii, const int32_t* jj, int64_t M, int L, int
                      cudaStream_t st)
 {
     k_all_keys<<<nblk(M, 256), 256, 0, st>>>(ii, jj, M, L, b, keys);
+}
+void launch_dot(const double* a, const double* b, int64_t n, double* part, int nblocks, double* out,
+                cudaStream_t st)
+{
+    k_dot<<<nblocks, 256, 0, st>>>(a, b, n, part);
+    k_reduce_single<<<1, 1024, 0, st>>>(part, nblocks, out);
+}
+void launch_axpby(double* y, double a, const double* x, double b, const double* z, int64_t n, cudaStream_t st)
+{
+    if (n > 0) k_axpby<<<nblk(n, 256), 256, 0, st>>>(y, a, x, b, z, n);
 }
 void launch_add_u64(unsigned long long* dst, const unsigned long long* src, cudaStream_t st)
 {

@@ -122,6 +122,11 @@ def test_one_sweep_parity(request, which, prec):
     if prec == bfc.PREC_FP64:
         # with lambda > 0 every block is strictly convex: the factors are unique
         assert rel_dev(Xg, Xo) <= 1e-7
+    # kernels per sweep: 1 + L right environments, 3 + 3 outer fiber kernels,
+    # per middle level Gram + solve (+ FP64 fallback + counter in the
+    # precision form), residual reduction, 2 for ||S||^2, 2 for the test error
+    per_level = 4 if prec == bfc.PREC_C64 else 2
+    assert st["launches"] == 12 + (1 + per_level) * p.L
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -310,3 +315,25 @@ def test_full_size_sampled_blocks_are_optimal(cfg3):
             f_opt = block_objective(A, p.t[sel], p.lam, s_opt)
             f_gpu = block_objective(A, p.t[sel], p.lam, Zn[m - 1, k].ravel())
             assert f_gpu <= f_opt * (1 + 1e-4) + 1e-12
+
+
+# ---------------------------------------------------------------- L-BFGS
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_lbfgs_parity(cfg2s, prec):
+    p, X0 = cfg2s
+    iters = 8
+    Xo, fo = oracle.lbfgs(p.n, p.L, p.b, p.r, p.lam, X0, p.i, p.j, p.t, iters)
+    with make(p, prec) as c:
+        c.set_factors(X0)
+        hist = c.lbfgs(iters)
+        Xg = c.get_factors()
+    fg = [h["objective"] for h in hist]
+    assert len(fg) == iters
+    assert all(b_ <= a_ * (1 + 1e-6) for a_, b_ in zip(fg[:-1], fg[1:]))
+    if prec == bfc.PREC_FP64:
+        np.testing.assert_allclose(fg, fo, rtol=1e-8)
+        assert rel_dev(Xg, Xo) <= 1e-6
+    else:
+        # complex64 gradients: the trajectory agrees to the gradient precision
+        np.testing.assert_allclose(fg, fo, rtol=1e-3)

@@ -365,3 +365,19 @@ def test_lowrank_start_quality_matches_paper_remark():
     tr = oracle.rel_err(p.n, p.L, p.b, p.r, X, p.i, p.j, p.t)
     te = oracle.rel_err(p.n, p.L, p.b, p.r, X, p.it, p.jt, p.tt)
     assert 0.5 < tr < 1.0 and 0.5 < te < 1.2
+
+
+def test_lbfgs_monotone_and_reaches_stationarity():
+    # Armijo line search: the objective never increases; a correct two-loop
+    # direction drives the gradient norm down by orders of magnitude.
+    n, L, b, r = 32, 2, 8, 2
+    lam = 1e-3
+    packed, i, j = small_problem(n, L, b, r, seed=12, n_obs=400)
+    t = synth.helmholtz_line(n, 15.0, 1.0, i, j)
+    g0, f0 = oracle.grad(n, L, b, r, lam, packed, i, j, t)
+    X, hist = oracle.lbfgs(n, L, b, r, lam, packed, i, j, t, 120)
+    assert hist[0] < f0
+    assert all(b_ <= a_ * (1 + 1e-12) for a_, b_ in zip(hist[:-1], hist[1:]))
+    g, f = oracle.grad(n, L, b, r, lam, X, i, j, t)
+    assert abs(f - hist[-1]) <= 1e-12 * abs(f)
+    assert np.linalg.norm(g) < 1e-3 * np.linalg.norm(g0)
