@@ -48,6 +48,7 @@ WORKLOAD = ("n=65536 L=12 b=16 r=8, exp(i w rho)/rho line-to-line kernel, w=pi n
             "|Omega|=4 n log2 n (3774874 train / 419430 test), lambda=1e-7")
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
+TC_FLOPS_PER_ENTRY = 2 * 3 * 128 * 80 * 2   # flop, 2 positions x M 128 x N 80 x 3 products
 
 
 def load_peaks():
@@ -126,11 +127,11 @@ def als_flops_per_entry(r: int) -> int:
     return 8 * (r * r * (r * r + 1) // 2 + r * r)
 
 
-def lowrank_start(prob, bfc_mod, prec):
+def lowrank_start(prob, bfc_mod, prec, gram=0):
     import synth
     A0, B0 = synth.random_lowrank_start(prob, prob.r)
     c = bfc_mod.Completion(prob.n, prob.L, prob.b, prob.r, prob.lam, prob.i, prob.j, prob.t,
-                           prob.it, prob.jt, prob.tt, prec=prec)
+                           prob.it, prob.jt, prob.tt, prec=prec, gram_impl=gram)
     c.lowrank_init(A0, B0, 10)
     return c
 
@@ -247,7 +248,7 @@ def run_bfc(args, rank, world, local_rank):
         f"(profiling case, {prob.nnz} train entries)")
     prec = bfc.PREC_C64 if args.prec == "c64" else bfc.PREC_FP64
 
-    c = lowrank_start(prob, bfc, prec)
+    c = lowrank_start(prob, bfc, prec, gram=bfc.GRAM_TENSOR if args.gram == "tensor" else bfc.GRAM_CUDA)
     stream = torch.cuda.Stream(device=dev)
     bfc.bfc_set_stream(c.ctx, stream.cuda_stream)
 
@@ -308,20 +309,38 @@ def run_bfc(args, rank, world, local_rank):
     mid_avg_ms = mid_ms / mid_n
     flops_per_launch = prob.nnz * als_flops_per_entry(prob.r)
     clocks = clk.summary()
-    sm_max = load_peaks().get("sm_max_mhz", 2070.0)
-    peak_tflops = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peaks = load_peaks()
     achieved = flops_per_launch / (mid_avg_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": "k_mid_gram (per-slice normal equations, one launch per middle level)",
-                "launch_ms": mid_avg_ms, "flop_per_launch": flops_per_launch,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+    tensor_gram = prec == bfc.PREC_C64 and args.gram == "tensor" and prob.r <= 8
+    if tensor_gram:
+        # tcgen05 kind::tf32: the contraction's own peak is the measured
+        # sustained bf16 peak (the kernel runs inside a long step) scaled by
+        # the nominal dense TF32 / BF16 ratio 1.1 / 2.25
+        peak_tflops = peaks.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25
+        executed = prob.nnz * TC_FLOPS_PER_ENTRY / (mid_avg_ms * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tflops, "traffic": None,
+                    "kernel": "k_mid_gram_tc (tcgen05 per-slice normal equations, one launch per middle level)",
+                    "launch_ms": mid_avg_ms, "flop_per_launch": flops_per_launch,
+                    "peak_source": "MEASURED_PEAKS bf16_tflops_sustained x 1.1/2.25 (of measured)",
+                    "executed_tflops": executed, "executed_frac": executed / peak_tflops,
+                    "executed_note": "issued MMA flops: 128 x 80 real embedding of the complex Gram "
+                                     "(Re and Im, full square, 2 contraction positions per entry) x 3 TF32 "
+                                     "split products = 122880 flop per entry"}
+    else:
+        sm_max = peaks.get("sm_max_mhz", 2070.0)
+        peak_tflops = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tflops, "traffic": None,
+                    "kernel": "k_mid_gram (per-slice normal equations, one launch per middle level)",
+                    "launch_ms": mid_avg_ms, "flop_per_launch": flops_per_launch,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64+f64" if prec == bfc.PREC_C64 else "f64",
             "data": "synthetic",
-            "config": {"workload": workload, "precision": args.prec,
+            "config": {"workload": workload, "precision": args.prec, "gram": args.gram,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "working set > L2 (no flush)", "nnz_train": prob.nnz},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * P,
@@ -372,6 +391,8 @@ def main():
     ap.add_argument("--prec", default="c64", choices=["c64", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance runs")
+    ap.add_argument("--gram", default="tensor", choices=["tensor", "cuda"],
+                    help="precision-form middle-level Gram: tcgen05 tensor cores or CUDA cores")
     ap.add_argument("--n", type=int, default=0,
                     help="reduced n with the same construction (small profiling captures only)")
     args = ap.parse_args()

@@ -98,6 +98,11 @@ typedef struct {
                                0 selects the default (2^-20, the complex64
                                rounding level of the normal equations, in the
                                precision form; none in FP64); < 0 disables  */
+    int32_t gram_impl;      /* precision form, per-slice normal equations of
+                               the middle levels: 0 = tensor cores (tcgen05,
+                               three-term TF32 products, Kahan-folded every
+                               32 entries) for r <= 8 and CUDA cores for
+                               r > 8; 1 = CUDA cores (complex64 FMA) always */
 } bfc_params;
 
 typedef struct {

@@ -30,6 +30,8 @@ __all__ = [
 
 PREC_FP64 = 0
 PREC_C64 = 1
+GRAM_TENSOR = 0   # tcgen05 Gram for r <= 8 in the precision form
+GRAM_CUDA = 1     # CUDA-core Gram always
 STATUS = {0: "BFC_OK", 1: "BFC_EINVAL", 2: "BFC_ENOMEM", 3: "BFC_ECUDA", 4: "BFC_ESINGULAR",
           5: "BFC_ETIMEOUT", 6: "BFC_ENONFINITE"}
 
@@ -54,7 +56,8 @@ class Params(ctypes.Structure):
                 ("max_sweeps", ctypes.c_int32), ("tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("init_kind", ctypes.c_int32), ("lr_rank", ctypes.c_int32),
                 ("lr_sweeps", ctypes.c_int32), ("values_on_device", ctypes.c_int32),
-                ("refine_sweeps", ctypes.c_int32), ("ridge_rel", ctypes.c_double)]
+                ("refine_sweeps", ctypes.c_int32), ("ridge_rel", ctypes.c_double),
+                ("gram_impl", ctypes.c_int32)]
 
 
 class SweepStats(ctypes.Structure):
@@ -280,11 +283,12 @@ class Completion:
 
     def __init__(self, n, L, b, r, lam, i, j, t, it=None, jt=None, tt=None, prec=PREC_FP64,
                  max_sweeps=20, tol=1e-3, seed=0, init_kind=0, lr_rank=0, lr_sweeps=10,
-                 refine_sweeps=0, ridge_rel=0.0):
+                 refine_sweeps=0, ridge_rel=0.0, gram_impl=GRAM_TENSOR):
         self.n, self.L, self.b, self.r = int(n), int(L), int(b), int(r)
         self.params = Params(n=n, L=L, b=b, r=r, lam=lam, prec=prec, max_sweeps=max_sweeps, tol=tol,
                              seed=seed, init_kind=init_kind, lr_rank=lr_rank, lr_sweeps=lr_sweeps,
-                             values_on_device=0, refine_sweeps=refine_sweeps, ridge_rel=ridge_rel)
+                             values_on_device=0, refine_sweeps=refine_sweeps, ridge_rel=ridge_rel,
+                             gram_impl=gram_impl)
         self.P = bfc_num_params(n, L, b, r)
         self._nnz = len(i)
         self.ctx = bfc_create(self.params, i, j, t, it, jt, tt)

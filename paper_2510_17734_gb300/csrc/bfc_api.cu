@@ -174,6 +174,9 @@ static bfc_status build(Ctx* c, const Inputs& in)
 {
     const int64_t N = c->N, n = c->n, S = c->S;
     const int L = c->L, r = c->r;
+    int dev = 0;
+    BFC_CK(c, cudaGetDevice(&dev));
+    BFC_CK(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
     BFC_CK(c, cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
     c->stream = c->own_stream;
     BFC_CK(c, cudaEventCreate(&c->ev0));
@@ -195,6 +198,7 @@ static bfc_status build(Ctx* c, const Inputs& in)
     }
     BFC_TRY(dalloc(c, (void**)&c->d_scalars, 16 * sizeof(double), "scalars"));
     BFC_TRY(dalloc(c, (void**)&c->d_count, 8 * sizeof(unsigned long long), "counters"));
+    BFC_CK(c, cudaMemsetAsync(c->d_count, 0, 8 * sizeof(unsigned long long), c->stream));
     c->red_cap = std::max<int64_t>(2 * n, 8192);
     BFC_TRY(dalloc(c, (void**)&c->d_red, c->red_cap * sizeof(double), "reduction"));
 
@@ -310,6 +314,7 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
     if (!isfinite(p.ridge_rel)) return fail(nullptr, BFC_EINVAL, "ridge_rel must be finite");
     if (p.prec != BFC_PREC_FP64 && p.prec != BFC_PREC_C64_FP64SOLVE)
         return fail(nullptr, BFC_EINVAL, "unknown precision");
+    if (p.gram_impl != 0 && p.gram_impl != 1) return fail(nullptr, BFC_EINVAL, "gram_impl must be 0 or 1");
     if (in.nnz <= 0 || in.nnz >= ((int64_t)1 << 31) - 1) return fail(nullptr, BFC_EINVAL, "nnz must be in [1, 2^31-2]");
     if (in.ntest < 0 || in.ntest >= ((int64_t)1 << 31) - 1) return fail(nullptr, BFC_EINVAL, "bad ntest");
     if (!in.i || !in.j || !in.t) return fail(nullptr, BFC_EINVAL, "null training data");
@@ -327,6 +332,7 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
     c->fp32 = p.prec == BFC_PREC_C64_FP64SOLVE;
     c->vsz = c->fp32 ? 8 : 16;
     c->ridge = p.ridge_rel > 0.0 ? p.ridge_rel : (p.ridge_rel == 0.0 && c->fp32 ? 9.5367431640625e-07 : 0.0);
+    c->gram_tc = c->fp32 && p.gram_impl == 0 && p.r <= 8;
     bfc_status st = build(c, in);
     if (st != BFC_OK) {
         g_create_err = c->err;
@@ -342,10 +348,17 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
 static bfc_status collect_stats(Ctx* c, bfc_sweep_stats* out, float ms)
 {
     double hs[8];
-    unsigned long long hc[3];
+    unsigned long long hc[6];
     BFC_CK(c, cudaMemcpyAsync(hs, c->d_scalars, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    BFC_CK(c, cudaMemcpyAsync(hc, c->d_count, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    BFC_CK(c, cudaMemcpyAsync(hc, c->d_count, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
     BFC_TRY(sync(c));
+    if (hc[5] != 0) {
+        // a bounded wait inside the tensor-core Gram expired: the sweep's
+        // results are undefined; clear the flag so the context stays usable
+        BFC_CK(c, cudaMemsetAsync(c->d_count + 5, 0, sizeof(unsigned long long), c->stream));
+        BFC_TRY(sync(c));
+        return fail(c, BFC_ETIMEOUT, "tensor-core Gram: a bounded device wait expired");
+    }
     if (out) {
         out->sweep = c->sweeps_done;
         out->train_rel_err = hs[1] > 0 ? sqrt(hs[0] / hs[1]) : sqrt(hs[0]);

@@ -1,0 +1,504 @@
+// Tensor-core (tcgen05, kind::tf32) per-slice normal equations of one middle
+// level in the precision form: for every slice k of the level order,
+//     K = sum_e conj(a_e) a_e^T (lower triangle),   y = sum_e conj(a_e) t_e,
+// with a_e = h_e (x) w_e (a[p R + c] = h_p w_c), the left and right
+// environments of entry e (Alg. 1, middle factors; Eq. (BF_tensor_rep)
+// read as a linear function of one slice).  Same output record as the
+// CUDA-core k_mid_gram: K packed lower-triangular, then y.
+//
+// Real form of the complex sums.  Write a = u + i v and give every entry two
+// positions on the contraction axis (part 0, part 1).  With the rows
+//     P_q = (u_q, v_q),   Q_p = (v_p, -u_p),   T = (Re t, Im t),
+//     Re K[p][q] = P_p . P_q,   Im K[p][q] = -(Q_p . P_q),
+//     Re y[p]    = P_p . T,     Im y[p]    = -(Q_p . T).
+// Shared memory holds the rows in the order Q (64 rows) | P (64) | T (1) |
+// zeros (15), so one MMA with A = rows 0..127 (M = 128) and B = rows
+// 64..143 (N = 80) produces all of them: D[p][q] = -Im K, D[64+p][q] = Re K,
+// column 64 the two parts of y.
+//
+// Precision: every operand is split into TF32 parts, x = hi + lo, and the
+// product is taken as hi*hi + (lo*hi + hi*lo) (three MMAs), which keeps it to
+// about FP32 accuracy.  The tensor core's FP32 accumulation into D
+// truncates: every update loses about 2^-24 |D| towards zero, a bias that
+// grows with the number of updates into one accumulator (measured on the
+// diagonal of K: -1.2e-6 relative with all three products of two chunks in
+// one accumulator, enough to stall ALS near 1e-3 test error).  So hi*hi goes
+// to its own accumulator (8 updates per chunk), the cross terms to another,
+// and both are folded into per-thread Kahan sums after every chunk (FOLD =
+// 1, SEP = 1: -4e-7, and the sweeps follow the FP64 trajectory).
+//
+// Roles (one persistent CTA of 17 warps per SM; slices round-robin):
+//   warps 0..15  load h, w, t of chunk g+1 into registers, build the TF32
+//                operand rows of chunk g in operand stage g&1, signal
+//                full[g&1]; then fold the accumulators of the group of FOLD
+//                chunks that ended at chunk g-1 into the Kahan sums
+//                (tcgen05.ld), signal accempty, and write the record when
+//                that group ended its slice (through a shared-memory
+//                scratch, so the global stores are coalesced)
+//   warp 16      waits full[s] (and accempty for a new group), issues the 24
+//                MMAs of the chunk into the accumulators of slot grp % NSLOT,
+//                commits to empty[s] and, at a group's end, to accfull; with
+//                PF > 0 it also prefetches the inputs of the chunk PF ahead
+//                into L2
+// Every mbarrier wait is bounded; on expiry the kernel raises *err, after
+// which all waits return at once (the work still runs to its end with the
+// same control flow in every warp, results undefined), then waits (bounded)
+// for its MMAs, frees its TMEM and returns.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bfc {
+
+struct TcGram {
+    static constexpr int CE = 32;                 // entries per chunk (one K block of 32 TF32)
+    static constexpr int ROWS = 144;              // Q 0..63 | P 64..127 | T 128 | zeros
+    static constexpr int KB = ROWS * 128;         // one K block: 144 rows x 128 B (SW128 atoms)
+    static constexpr int STAGE = 4 * KB;          // [part][hi/lo] K blocks
+    static constexpr int NCOL = 80;               // accumulator columns (N)
+    static constexpr int NACC = 4;                // TMEM accumulators, 128 columns apart
+    static constexpr int TMEM_COLS = 512;
+    static constexpr int NBUILD = 16;             // builder / fold warps: 4 per TMEM lane quadrant
+    static constexpr int NTH = 32 * (NBUILD + 1); // + the MMA warp
+    static constexpr int SCR_LD = 81;             // record scratch row stride (floats)
+    static constexpr int SCR = 128 * SCR_LD * 4;  // record scratch: 128 lanes x 80 columns
+    static constexpr int SEGC = 1024;             // cached (start, end) of this CTA's first slices
+    static constexpr size_t SMEM = 1024 + 2 * (size_t)STAGE + SCR + 8 * (size_t)SEGC + 128;
+    static constexpr uint32_t WAIT_LIMIT = 1u << 22;
+    static constexpr int PF_AHEAD = 0;            // chunks of input prefetched into L2 ahead (0: off)
+    static constexpr int FOLD = 1;                // chunks per TMEM accumulation between Kahan folds
+    static constexpr int SEP = 1;                 // separate accumulators for hi*hi and the cross terms
+};
+
+__device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle (8-row atoms of
+// 1024 bytes, 16-byte chunks permuted by the row within the atom), 8-row
+// groups 1024 bytes apart.  The address field is the low 14 bits (address
+// >> 4), so adding (offset >> 4) to a descriptor moves it by `offset` bytes.
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;              // leading-dimension offset (not used with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;    // stride offset between 8-row groups
+    d |= (uint64_t)1 << 46;              // descriptor version
+    d |= (uint64_t)2 << 61;              // 128-byte swizzle
+    return d;
+}
+
+// x = hi + lo with hi and lo TF32 numbers (10 explicit mantissa bits; the
+// low 13 bits of the pattern are zero).  Each part is rounded to nearest
+// (ties away from zero) by adding half a unit of the 13 dropped bits to
+// the pattern and masking; x - hi is exact in FP32, so |x - hi - lo| <=
+// 2^-23 |x|.
+__device__ __forceinline__ void tc_split(float x, uint32_t& hi, uint32_t& lo)
+{
+    hi = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+    const float r = x - __uint_as_float(hi);
+    lo = (__float_as_uint(r) + 0x1000u) & 0xFFFFE000u;
+}
+
+__device__ __forceinline__ bool tc_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the completion of phase `parity` of an mbarrier.  Returns
+// at once when *abort is set; sets *abort and *err when the limit expires.
+__device__ __forceinline__ void tc_wait(uint32_t bar, uint32_t parity, volatile int* abort,
+                                        unsigned long long* err)
+{
+    if (*abort) return;
+    for (uint32_t it = 0; it < TcGram::WAIT_LIMIT; ++it)
+        if (tc_try_wait(bar, parity)) return;
+    *abort = 1;
+    atomicExch(err, 1ull);
+}
+
+__device__ __forceinline__ void tc_arrive(uint32_t bar)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+
+// Consecutive accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tc_ld4(uint32_t taddr, float* v)
+{
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+struct TcChunk {
+    int k, base, cnt, s1;
+    int idx;    // chunk index within the slice; FOLD consecutive chunks form a group
+    int grp;    // group number within the CTA; accumulator slot grp % NSLOT
+    bool valid, last;
+};
+
+// Rank R <= 8 (D = R^2 <= 64 features).  Records of empty slices are zero.
+// FOLD: chunks accumulated in TMEM between Kahan folds.  SEP: hi*hi and
+// the two cross products go to separate accumulators.  PF: chunks of input
+// prefetched into L2 ahead of the builders (0: none).
+template <int R, int FOLD = TcGram::FOLD, int SEP = TcGram::SEP, int PF = TcGram::PF_AHEAD>
+__global__ void __launch_bounds__(TcGram::NTH, 1)
+k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const float2* __restrict__ tv,
+              const int32_t* __restrict__ seg, float2* __restrict__ rec, int S, unsigned long long* err)
+{
+    static_assert(R >= 1 && R <= 8, "tensor-core Gram needs R*R <= 64");
+    static_assert(FOLD >= 1 && (SEP == 0 || SEP == 1), "bad accumulation layout");
+    constexpr int D = R * R, NPK = D * (D + 1) / 2, CE = TcGram::CE;
+    constexpr int NSLOT = TcGram::NACC / (1 + SEP);   // accumulator groups in flight
+    constexpr int NB = 32 * TcGram::NBUILD;   // builder threads
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw_s = tc_smem_u32(smem_raw);
+    unsigned char* ops = smem_raw + ((1024u - (raw_s & 1023u)) & 1023u);  // 2 operand stages
+    float* scr = (float*)(ops + 2 * TcGram::STAGE);                        // record scratch
+    int2* segc = (int2*)((unsigned char*)scr + TcGram::SCR);               // slice bounds cache
+    uint64_t* bars = (uint64_t*)(segc + TcGram::SEGC);
+    uint64_t* full = bars;            // [2]  builders -> MMA warp (count NBUILD)
+    uint64_t* empty = bars + 2;       // [2]  MMA commit -> builders
+    uint64_t* accfull = bars + 4;     // [NSLOT]  MMA commit at a group's end -> builders
+    uint64_t* accempty = bars + 8;    // [NSLOT]  builders' fold -> MMA warp (count NBUILD)
+    uint32_t* tmem_slot = (uint32_t*)(bars + 12);
+    volatile int* abort_s = (volatile int*)(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // zero both operand stages (rows never written stay zero) and the
+    // records of this CTA's empty slices
+    for (int x = tid; x < 2 * TcGram::STAGE / 16; x += TcGram::NTH) ((uint4*)ops)[x] = make_uint4(0, 0, 0, 0);
+    for (int k = blockIdx.x; k < S; k += gridDim.x)
+        if (seg[k + 1] == seg[k])
+            for (int x = tid; x < NPK + D; x += TcGram::NTH)
+                rec[(size_t)k * (NPK + D) + x] = make_float2(0.f, 0.f);
+    for (int i = tid; i < TcGram::SEGC; i += TcGram::NTH) {
+        const int k = blockIdx.x + i * gridDim.x;
+        if (k >= S) break;
+        segc[i] = make_int2(seg[k], seg[k + 1]);
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 12; ++i) {
+            const uint32_t cnt = (i < 2 || i >= 8) ? (uint32_t)TcGram::NBUILD : 1u;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem_u32(&bars[i])), "r"(cnt));
+        }
+        *abort_s = 0;
+    }
+    __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(tc_smem_u32(tmem_slot)), "n"(TcGram::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    // chunk enumeration (identical in every warp)
+    auto first_of = [&](int k, int grp) {
+        TcChunk c;
+        c.valid = false;
+        for (; k < S; k += gridDim.x) {
+            const int i = (k - (int)blockIdx.x) / (int)gridDim.x;
+            int s0, s1;
+            if (i < TcGram::SEGC) {
+                const int2 sb = segc[i];
+                s0 = sb.x; s1 = sb.y;
+            } else {
+                s0 = seg[k]; s1 = seg[k + 1];
+            }
+            if (s1 > s0) {
+                c.k = k; c.base = s0; c.s1 = s1; c.cnt = min(CE, s1 - s0);
+                c.idx = 0; c.grp = grp;
+                c.last = s0 + CE >= s1; c.valid = true;
+                break;
+            }
+        }
+        return c;
+    };
+    auto advance = [&](const TcChunk& c) {
+        if (!c.last) {
+            TcChunk n = c;
+            n.base = c.base + CE;
+            n.cnt = min(CE, c.s1 - n.base);
+            n.last = n.base + CE >= c.s1;
+            n.idx = c.idx + 1;
+            n.grp = (n.idx % FOLD) ? c.grp : c.grp + 1;
+            return n;
+        }
+        return first_of(c.k + gridDim.x, c.grp + 1);
+    };
+
+    if (warp == TcGram::NBUILD) {
+        // ------------------------------------------------------------ MMA warp
+        if (lane == 0) {
+            constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) |
+                                       ((uint32_t)(TcGram::NCOL >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+            const uint64_t desc0 = tc_sdesc(tc_smem_u32(ops));
+            // L2 prefetch of the inputs of the chunk PF_AHEAD chunks ahead
+            // (16-byte aligned ranges, clipped to the level's entries)
+            const uint64_t h_end = ((uint64_t)seg[S] * R * 8) & ~(uint64_t)15;
+            const uint64_t t_end = ((uint64_t)seg[S] * 8) & ~(uint64_t)15;
+            auto prefetch = [&](const TcChunk& c) {
+                auto range = [&](const void* base, uint64_t b0, uint64_t b1, uint64_t end) {
+                    b0 &= ~(uint64_t)15;
+                    b1 = (b1 + 15) & ~(uint64_t)15;
+                    if (b1 > end) b1 = end;
+                    if (b1 > b0)
+                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                                     ::"l"((const char*)base + b0), "r"((uint32_t)(b1 - b0))
+                                     : "memory");
+                };
+                range(H, (uint64_t)c.base * R * 8, (uint64_t)(c.base + c.cnt) * R * 8, h_end);
+                range(Wm, (uint64_t)c.base * R * 8, (uint64_t)(c.base + c.cnt) * R * 8, h_end);
+                range(tv, (uint64_t)c.base * 8, (uint64_t)(c.base + c.cnt) * 8, t_end);
+            };
+            TcChunk pf = first_of(blockIdx.x, 0);
+            if (PF == 0) pf.valid = false;
+            for (int i = 0; i < PF && pf.valid; ++i) {
+                prefetch(pf);
+                pf = advance(pf);
+            }
+            int g = 0;
+            for (TcChunk c = first_of(blockIdx.x, 0); c.valid; c = advance(c), ++g) {
+                const int b = g & 1, slot = c.grp % NSLOT;
+                if (pf.valid) {
+                    prefetch(pf);
+                    pf = advance(pf);
+                }
+                tc_wait(tc_smem_u32(&full[b]), (uint32_t)((g >> 1) & 1), abort_s, err);
+                const bool fresh = c.idx % FOLD == 0;   // the first chunk of a group overwrites D
+                if (fresh && c.grp >= NSLOT)
+                    tc_wait(tc_smem_u32(&accempty[slot]), (uint32_t)((c.grp / NSLOT - 1) & 1), abort_s, err);
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (*abort_s) continue;
+                const uint32_t d_big = tmem + (uint32_t)(slot * (1 + SEP) * 128);
+                const uint32_t d_small = d_big + (SEP ? 128u : 0u);
+                const uint64_t sd = desc0 + (uint64_t)((b * TcGram::STAGE) >> 4);
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint64_t a_hi = sd + (uint64_t)(((2 * part) * TcGram::KB + ks * 32) >> 4);
+                        const uint64_t a_lo = a_hi + (uint64_t)(TcGram::KB >> 4);
+                        const uint64_t b_hi = a_hi + (uint64_t)((64 * 128) >> 4);
+                        const uint64_t b_lo = a_lo + (uint64_t)((64 * 128) >> 4);
+                        const uint64_t A[3] = {a_lo, a_hi, a_hi};
+                        const uint64_t B[3] = {b_hi, b_lo, b_hi};
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) {
+                            // t = 2 is hi*hi; with SEP the cross terms t = 0, 1 go to d_small
+                            const bool big = SEP ? t == 2 : true;
+                            const bool first = fresh && part == 0 && ks == 0 && (SEP ? (t == 0 || t == 2) : t == 0);
+                            const uint32_t en = first ? 0u : 1u;
+                            asm volatile(
+                                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(big ? d_big : d_small),
+                                "l"(A[t]), "l"(B[t]), "r"(IDESC), "r"(en));
+                        }
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(tc_smem_u32(&empty[b]))
+                             : "memory");
+                if (c.idx % FOLD == FOLD - 1 || c.last)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 ::"r"(tc_smem_u32(&accfull[slot]))
+                                 : "memory");
+            }
+            if (*abort_s && g >= 1) {
+                // let the issued MMAs drain (bounded) before the TMEM is freed
+                for (uint32_t it = 0; it < TcGram::WAIT_LIMIT; ++it)
+                    if (tc_try_wait(tc_smem_u32(&empty[(g - 1) & 1]), (uint32_t)(((g - 1) >> 1) & 1))) break;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------- builder warps
+        // Kahan sums of this thread's accumulator lane and columns: warp w
+        // reads TMEM lanes 32 (w & 3) .. +31; column group cg = w >> 2 owns
+        // columns 16 cg .. 16 cg + 15 and 64 + 4 cg .. 64 + 4 cg + 3.
+        const int row = 32 * (warp & 3) + lane;
+        const int cg = warp >> 2;
+        float sum[20], comp[20];
+#pragma unroll
+        for (int j = 0; j < 20; ++j) { sum[j] = 0.f; comp[j] = 0.f; }
+        auto col_of = [&](int j) { return j < 16 ? 16 * cg + j : 64 + 4 * cg + (j - 16); };
+
+        auto fold = [&](const TcChunk& c) {
+            const int slot = c.grp % NSLOT;
+            tc_wait(tc_smem_u32(&accfull[slot]), (uint32_t)((c.grp / NSLOT) & 1), abort_s, err);
+            __syncwarp();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float v[20];
+            const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(slot * (1 + SEP) * 128);
+            tc_ld16(ta + 16 * cg, v);
+            tc_ld4(ta + 64 + 4 * cg, v + 16);
+            if (SEP) {
+                float w[20];
+                tc_ld16(ta + 128 + 16 * cg, w);
+                tc_ld4(ta + 128 + 64 + 4 * cg, w + 16);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 20; ++j) v[j] += w[j];
+            } else {
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tc_arrive(tc_smem_u32(&accempty[slot]));
+#pragma unroll
+            for (int j = 0; j < 20; ++j) {
+                const float y = v[j] - comp[j];
+                const float t = sum[j] + y;
+                comp[j] = (t - sum[j]) - y;
+                sum[j] = t;
+            }
+            if (c.last) {
+                // corrected sums -> scratch -> coalesced record stores
+#pragma unroll
+                for (int j = 0; j < 20; ++j) {
+                    scr[row * TcGram::SCR_LD + col_of(j)] = sum[j] - comp[j];
+                    sum[j] = 0.f;
+                    comp[j] = 0.f;
+                }
+                asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
+                float2* out = rec + (size_t)c.k * (NPK + D);
+                for (int x = tid; x < NPK; x += NB) {
+                    int p = (int)((sqrtf(8.f * (float)x + 1.f) - 1.f) * 0.5f);
+                    while ((p + 1) * (p + 2) / 2 <= x) ++p;
+                    while (p * (p + 1) / 2 > x) --p;
+                    const int q = x - p * (p + 1) / 2;
+                    out[x] = make_float2(scr[(64 + p) * TcGram::SCR_LD + q], -scr[p * TcGram::SCR_LD + q]);
+                }
+                for (int p = tid; p < D; p += NB)
+                    out[NPK + p] =
+                        make_float2(scr[(64 + p) * TcGram::SCR_LD + 64], -scr[p * TcGram::SCR_LD + 64]);
+                asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
+            }
+        };
+
+        // operand rows of this thread: entry e = lane, rows q = r8 + 8 j
+        // (j = jb .. jb + 3) with r8 = w & 7, so the swizzled offset inside a
+        // row group is fixed per thread
+        const int r8 = warp & 7, jb = 4 * (warp >> 3);
+        const uint32_t t_off = (uint32_t)(r8 * 128 + ((((lane >> 2) ^ r8)) << 4) + (lane & 3) * 4);
+        const int e = lane;
+
+        // the h_p, w_c (and t) this thread needs for chunk c, in registers
+        // (rank 8: p = j and c = r8, so one w and four consecutive h)
+        constexpr int NW = R == 8 ? 1 : 4;
+        struct Vals { float2 h[4], w[NW], t; };
+        auto load = [&](const TcChunk& c, Vals& vl) {
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) vl.h[jj] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int jj = 0; jj < NW; ++jj) vl.w[jj] = make_float2(0.f, 0.f);
+            vl.t = make_float2(0.f, 0.f);
+            if (!c.valid || e >= c.cnt) return;
+            const size_t ent = (size_t)(c.base + e);
+            if (R == 8) {
+                const float4* hp = (const float4*)(H + ent * R + jb);
+                const float4 h01 = __ldg(hp), h23 = __ldg(hp + 1);
+                vl.h[0] = make_float2(h01.x, h01.y);
+                vl.h[1] = make_float2(h01.z, h01.w);
+                vl.h[2] = make_float2(h23.x, h23.y);
+                vl.h[3] = make_float2(h23.z, h23.w);
+                vl.w[0] = __ldg(Wm + ent * R + r8);
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int q = r8 + 8 * (jb + jj);
+                    if (q < D) {
+                        vl.h[jj] = __ldg(H + ent * R + q / R);
+                        vl.w[jj % NW] = __ldg(Wm + ent * R + q % R);
+                    }
+                }
+            }
+            if (warp == 0) vl.t = __ldg(tv + ent);
+        };
+
+        TcChunk cur = first_of(blockIdx.x, 0), prev;
+        prev.valid = false;
+        Vals vc, vn;
+        load(cur, vc);
+        int g = 0;
+        while (cur.valid) {
+            const TcChunk nxt = advance(cur);
+            load(nxt, vn);   // the next chunk's values are in flight during this chunk
+            const int b = g & 1;
+            if (g >= 2) tc_wait(tc_smem_u32(&empty[b]), (uint32_t)(((g - 2) >> 1) & 1), abort_s, err);
+            unsigned char* st = ops + b * TcGram::STAGE;
+            auto put = [&](uint32_t off, int part, uint32_t hi, uint32_t lo) {
+                *(uint32_t*)(st + (2 * part) * TcGram::KB + off) = hi;
+                *(uint32_t*)(st + (2 * part + 1) * TcGram::KB + off) = lo;
+            };
+            if (warp == 0) {  // T row 128 (row group 16, r8 = 0)
+                uint32_t h0, l0, h1, l1;
+                tc_split(vc.t.x, h0, l0);
+                tc_split(vc.t.y, h1, l1);
+                put(16 * 1024 + t_off, 0, h0, l0);
+                put(16 * 1024 + t_off, 1, h1, l1);
+            }
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int j = jb + jj;
+                const int q = r8 + 8 * j;
+                if (q < D) {
+                    const float2 hv = vc.h[jj], wq = vc.w[jj % NW];
+                    const float u = hv.x * wq.x - hv.y * wq.y;
+                    const float v = hv.x * wq.y + hv.y * wq.x;
+                    uint32_t uh, ul, vh, vl;
+                    tc_split(u, uh, ul);
+                    tc_split(v, vh, vl);
+                    const uint32_t offq = (uint32_t)(j * 1024) + t_off;
+                    put(offq + 8192, 0, uh, ul);                      // P_q = (u, v)
+                    put(offq + 8192, 1, vh, vl);
+                    put(offq, 0, vh, vl);                             // Q_q = (v, -u)
+                    put(offq, 1, uh ^ 0x80000000u, ul ^ 0x80000000u);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tc_arrive(tc_smem_u32(&full[b]));
+            if (prev.valid && (prev.idx % FOLD == FOLD - 1 || prev.last)) fold(prev);
+            prev = cur;
+            cur = nxt;
+            vc = vn;
+            ++g;
+        }
+        if (prev.valid) fold(prev);   // the last chunk always ends its group
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TcGram::TMEM_COLS));
+    }
+}
+
+}  // namespace bfc

@@ -36,6 +36,8 @@ struct Ctx {
     int L = 0, b = 0, r = 0;
     bool fp32 = false;              // compute type float (precision form) or double
     double ridge = 0.0;             // effective ridge floor factor (ridge_rel resolved)
+    bool gram_tc = false;           // middle-level Gram on the tensor cores (tcgen05)
+    int num_sms = 0;                // SMs of the context's device (persistent grids)
     size_t vsz = 16;                // bytes of one complex compute value
     cudaStream_t stream = nullptr, own_stream = nullptr;
     std::string err;

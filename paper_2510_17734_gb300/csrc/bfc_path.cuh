@@ -2,6 +2,7 @@
 // Each function only enqueues work on the context stream.
 #pragma once
 
+#include "bfc_gram_tc.cuh"
 #include "bfc_internal.h"
 #include "bfc_kernels.cuh"
 #include "bfc_util.h"
@@ -12,6 +13,16 @@ inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); 
 
 template <typename T, int R> struct Path {
     typedef typename cvec<T>::type V;
+    // the tensor-core Gram exists for the complex64 form with R * R <= 64
+    static constexpr bool TC = sizeof(T) == 4 && R <= 8;
+
+    static cudaError_t set_tc_attr()
+    {
+        if constexpr (TC)
+            return cudaFuncSetAttribute(k_mid_gram_tc<TC ? R : 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)TcGram::SMEM);
+        return cudaSuccess;
+    }
 
     static bfc_status configure(Ctx* c)
     {
@@ -23,6 +34,7 @@ template <typename T, int R> struct Path {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_mid_fallback<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SolveCfg<T, R>::SMEM);
+        if (e == cudaSuccess && TC) e = set_tc_attr();
         if (e != cudaSuccess)
             return fail(c, BFC_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
         return BFC_OK;
@@ -107,8 +119,19 @@ template <typename T, int R> struct Path {
             V* hout = m & 1 ? H1 : H0;
             {
                 ProfScope ps(c, "mid_gram");
-                k_mid_gram<T, R><<<(unsigned)S, GC::NTH, GC::SMEM, c->stream>>>(
-                    hin, W + (size_t)m * NR, (const V*)c->tval[m], c->seg[m], (V*)c->rec, (int)S);
+                bool done = false;
+                if constexpr (TC) {
+                    if (c->gram_tc) {
+                        const unsigned g = (unsigned)(S < c->num_sms ? S : c->num_sms);
+                        k_mid_gram_tc<TC ? R : 1><<<g, TcGram::NTH, TcGram::SMEM, c->stream>>>(
+                            (const float2*)hin, (const float2*)(W + (size_t)m * NR), (const float2*)c->tval[m],
+                            c->seg[m], (float2*)c->rec, (int)S, c->d_count + 5);
+                        done = true;
+                    }
+                }
+                if (!done)
+                    k_mid_gram<T, R><<<(unsigned)S, GC::NTH, GC::SMEM, c->stream>>>(
+                        hin, W + (size_t)m * NR, (const V*)c->tval[m], c->seg[m], (V*)c->rec, (int)S);
             }
             {
                 ProfScope ps(c, "mid_solve");

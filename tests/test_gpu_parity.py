@@ -129,6 +129,46 @@ def test_one_sweep_parity(request, which, prec):
     assert st["launches"] == 12 + (1 + per_level) * p.L
 
 
+@pytest.fixture(scope="module")
+def cfg3s():
+    # the n = 65536 workload's structure (b = 16, r = 8, 4 n log2 n samples)
+    # at n = 2048: the rank-8 middle levels run the 64-feature Gram
+    p = synth.config(3, n_override=2048)
+    return p, lr_start(p)
+
+
+@pytest.mark.parametrize("gram", [bfc.GRAM_TENSOR, bfc.GRAM_CUDA])
+def test_one_sweep_parity_rank8_gram_kernels(cfg3s, gram):
+    """Both middle-level Gram kernels of the precision form (tensor cores:
+    three-term TF32 products; CUDA cores: complex64 FMA) against the oracle
+    sweep, with the complex64 tolerance."""
+    p, X0 = cfg3s
+    Xo, st_o = oracle.als_sweep(p.n, p.L, p.b, p.r, p.lam, X0, p.i, p.j, p.t)
+    with make(p, bfc.PREC_C64, gram_impl=gram) as c:
+        c.set_factors(X0)
+        st = c.sweep()
+        Xg = c.get_factors()
+    tol = TOL[bfc.PREC_C64]
+    assert abs(st["objective"] - st_o["objective"]) <= tol * abs(st_o["objective"])
+    assert abs(st["train_rel_err"] - st_o["train_rel_err"]) <= tol * st_o["train_rel_err"]
+    for (ii, jj) in [(p.i, p.j), (p.it, p.jt)]:
+        xg = oracle.eval_entries(p.n, p.L, p.b, p.r, Xg, ii, jj)
+        xo = oracle.eval_entries(p.n, p.L, p.b, p.r, Xo, ii, jj)
+        assert rel_dev(xg, xo) <= 10 * tol
+
+
+def test_gram_kernels_agree_over_sweeps(cfg3s):
+    """Five sweeps with each Gram kernel follow the same trajectory."""
+    p, X0 = cfg3s
+    hist = {}
+    for gram in (bfc.GRAM_TENSOR, bfc.GRAM_CUDA):
+        with make(p, bfc.PREC_C64, gram_impl=gram) as c:
+            c.set_factors(X0)
+            hist[gram] = [c.sweep()["train_rel_err"] for _ in range(5)]
+    for a, b in zip(hist[bfc.GRAM_TENSOR], hist[bfc.GRAM_CUDA]):
+        assert abs(a - b) <= 1e-3 * b
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_ten_sweeps_cfg1_final_test_error(cfg1, prec):
     p, X0 = cfg1
