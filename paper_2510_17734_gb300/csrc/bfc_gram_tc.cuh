@@ -22,24 +22,26 @@
 // truncates: every update loses about 2^-24 |D| towards zero, a bias that
 // grows with the number of updates into one accumulator (measured on the
 // diagonal of K: -1.2e-6 relative with all three products of two chunks in
-// one accumulator, enough to stall ALS near 1e-3 test error).  So hi*hi goes
-// to its own accumulator (8 updates per chunk), the cross terms to another,
-// and both are folded into per-thread Kahan sums after every chunk (FOLD =
-// 1, SEP = 1: -4e-7, and the sweeps follow the FP64 trajectory).
+// one accumulator, enough to stall ALS near 1e-3 test error).  So every
+// chunk gets its own hi*hi accumulator (8 updates), folded into per-thread
+// Kahan sums, while the cross terms, 2^-11 smaller, run over the whole
+// slice in one accumulator (bias -4e-7; the sweeps follow the FP64
+// trajectory).  The first chunk of a slice puts all three products into its
+// hi*hi accumulator, so the cross-term accumulator of the previous slice can
+// still be read while the next slice starts.
 //
-// Roles (one persistent CTA of 17 warps per SM; slices round-robin):
-//   warps 0..15  load h, w, t of chunk g+1 into registers, build the TF32
+// Roles (one persistent CTA of 9 warps per SM; slices round-robin):
+//   warps 0..7   load h, w, t of chunk g+1 into registers, build the TF32
 //                operand rows of chunk g in operand stage g&1, signal
-//                full[g&1]; then fold the accumulators of the group of FOLD
-//                chunks that ended at chunk g-1 into the Kahan sums
-//                (tcgen05.ld), signal accempty, and write the record when
-//                that group ended its slice (through a shared-memory
-//                scratch, so the global stores are coalesced)
-//   warp 16      waits full[s] (and accempty for a new group), issues the 24
-//                MMAs of the chunk into the accumulators of slot grp % NSLOT,
-//                commits to empty[s] and, at a group's end, to accfull; with
-//                PF > 0 it also prefetches the inputs of the chunk PF ahead
-//                into L2
+//                full[g&1]; then fold the hi*hi accumulator of chunk g-2
+//                (two chunks late, so it is complete) into the Kahan sums
+//                (tcgen05.ld, lower triangle only), signal accempty, and at
+//                the end of a slice add its cross terms, signal sempty and
+//                write the record (through a shared-memory scratch, so the
+//                global stores are coalesced)
+//   warp 8       waits full[s] (and accempty / sempty when it reuses an
+//                accumulator), issues the 24 MMAs of the chunk, commits to
+//                empty[s] and accfull
 // Every mbarrier wait is bounded; on expiry the kernel raises *err, after
 // which all waits return at once (the work still runs to its end with the
 // same control flow in every warp, results undefined), then waits (bounded)
@@ -57,18 +59,16 @@ struct TcGram {
     static constexpr int KB = ROWS * 128;         // one K block: 144 rows x 128 B (SW128 atoms)
     static constexpr int STAGE = 4 * KB;          // [part][hi/lo] K blocks
     static constexpr int NCOL = 80;               // accumulator columns (N)
-    static constexpr int NACC = 4;                // TMEM accumulators, 128 columns apart
+    static constexpr int NBIG = 3;                // per-chunk hi*hi accumulators at TMEM columns 0, 128, 256
+    static constexpr int SMALL_COL = 384;         // per-slice cross-term accumulator
     static constexpr int TMEM_COLS = 512;
-    static constexpr int NBUILD = 16;             // builder / fold warps: 4 per TMEM lane quadrant
+    static constexpr int NBUILD = 8;              // builder / fold warps: 2 per TMEM lane quadrant
     static constexpr int NTH = 32 * (NBUILD + 1); // + the MMA warp
     static constexpr int SCR_LD = 81;             // record scratch row stride (floats)
     static constexpr int SCR = 128 * SCR_LD * 4;  // record scratch: 128 lanes x 80 columns
     static constexpr int SEGC = 1024;             // cached (start, end) of this CTA's first slices
     static constexpr size_t SMEM = 1024 + 2 * (size_t)STAGE + SCR + 8 * (size_t)SEGC + 128;
     static constexpr uint32_t WAIT_LIMIT = 1u << 22;
-    static constexpr int PF_AHEAD = 0;            // chunks of input prefetched into L2 ahead (0: off)
-    static constexpr int FOLD = 1;                // chunks per TMEM accumulation between Kahan folds
-    static constexpr int SEP = 1;                 // separate accumulators for hi*hi and the cross terms
 };
 
 __device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -140,6 +140,12 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v)
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
+__device__ __forceinline__ void tc_ld1(uint32_t taddr, float* v)
+{
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    v[0] = __uint_as_float(r);
+}
 __device__ __forceinline__ void tc_ld4(uint32_t taddr, float* v)
 {
     uint32_t r[4];
@@ -151,25 +157,29 @@ __device__ __forceinline__ void tc_ld4(uint32_t taddr, float* v)
 }
 
 struct TcChunk {
-    int k, base, cnt, s1;
-    int idx;    // chunk index within the slice; FOLD consecutive chunks form a group
-    int grp;    // group number within the CTA; accumulator slot grp % NSLOT
-    bool valid, last;
+    int k, base, s1;   // slice id, first entry of the chunk, end of the slice
+    int idx;           // chunk index within the slice
+    int sl;            // slice number within the CTA
+    bool valid;
+    __device__ __forceinline__ int cnt() const { return min(TcGram::CE, s1 - base); }
+    __device__ __forceinline__ bool last() const { return base + TcGram::CE >= s1; }
+};
+
+// A chunk waiting for its fold: CTA chunk number, slice, and whether it
+// ends the slice (then `multi`: the slice used the cross-term accumulator).
+struct TcFold {
+    int k, gc;
+    bool valid, last, multi;
 };
 
 // Rank R <= 8 (D = R^2 <= 64 features).  Records of empty slices are zero.
-// FOLD: chunks accumulated in TMEM between Kahan folds.  SEP: hi*hi and
-// the two cross products go to separate accumulators.  PF: chunks of input
-// prefetched into L2 ahead of the builders (0: none).
-template <int R, int FOLD = TcGram::FOLD, int SEP = TcGram::SEP, int PF = TcGram::PF_AHEAD>
+template <int R>
 __global__ void __launch_bounds__(TcGram::NTH, 1)
 k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const float2* __restrict__ tv,
               const int32_t* __restrict__ seg, float2* __restrict__ rec, int S, unsigned long long* err)
 {
     static_assert(R >= 1 && R <= 8, "tensor-core Gram needs R*R <= 64");
-    static_assert(FOLD >= 1 && (SEP == 0 || SEP == 1), "bad accumulation layout");
-    constexpr int D = R * R, NPK = D * (D + 1) / 2, CE = TcGram::CE;
-    constexpr int NSLOT = TcGram::NACC / (1 + SEP);   // accumulator groups in flight
+    constexpr int D = R * R, NPK = D * (D + 1) / 2, CE = TcGram::CE, NBIG = TcGram::NBIG;
     constexpr int NB = 32 * TcGram::NBUILD;   // builder threads
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw_s = tc_smem_u32(smem_raw);
@@ -177,17 +187,18 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
     float* scr = (float*)(ops + 2 * TcGram::STAGE);                        // record scratch
     int2* segc = (int2*)((unsigned char*)scr + TcGram::SCR);               // slice bounds cache
     uint64_t* bars = (uint64_t*)(segc + TcGram::SEGC);
-    uint64_t* full = bars;            // [2]  builders -> MMA warp (count NBUILD)
-    uint64_t* empty = bars + 2;       // [2]  MMA commit -> builders
-    uint64_t* accfull = bars + 4;     // [NSLOT]  MMA commit at a group's end -> builders
-    uint64_t* accempty = bars + 8;    // [NSLOT]  builders' fold -> MMA warp (count NBUILD)
-    uint32_t* tmem_slot = (uint32_t*)(bars + 12);
+    uint64_t* full = bars;            // [2]     builders -> MMA warp (count NBUILD)
+    uint64_t* empty = bars + 2;       // [2]     MMA commit -> builders (operand stage free)
+    uint64_t* accfull = bars + 4;     // [NBIG]  MMA commit -> builders (chunk accumulated)
+    uint64_t* accempty = bars + 7;    // [NBIG]  builders' fold -> MMA warp (count NBUILD)
+    uint64_t* sempty = bars + 10;     // [1]     builders read the cross terms -> MMA warp (count NBUILD)
+    uint32_t* tmem_slot = (uint32_t*)(bars + 11);
     volatile int* abort_s = (volatile int*)(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // zero both operand stages (rows never written stay zero) and the
-    // records of this CTA's empty slices
+    // records of this CTA's empty slices; cache the slice bounds
     for (int x = tid; x < 2 * TcGram::STAGE / 16; x += TcGram::NTH) ((uint4*)ops)[x] = make_uint4(0, 0, 0, 0);
     for (int k = blockIdx.x; k < S; k += gridDim.x)
         if (seg[k + 1] == seg[k])
@@ -199,8 +210,8 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
         segc[i] = make_int2(seg[k], seg[k + 1]);
     }
     if (tid == 0) {
-        for (int i = 0; i < 12; ++i) {
-            const uint32_t cnt = (i < 2 || i >= 8) ? (uint32_t)TcGram::NBUILD : 1u;
+        for (int i = 0; i < 11; ++i) {
+            const uint32_t cnt = (i < 2 || i >= 7) ? (uint32_t)TcGram::NBUILD : 1u;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem_u32(&bars[i])), "r"(cnt));
         }
         *abort_s = 0;
@@ -219,7 +230,7 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
     const uint32_t tmem = *tmem_slot;
 
     // chunk enumeration (identical in every warp)
-    auto first_of = [&](int k, int grp) {
+    auto first_of = [&](int k, int sl) {
         TcChunk c;
         c.valid = false;
         for (; k < S; k += gridDim.x) {
@@ -232,72 +243,44 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
                 s0 = seg[k]; s1 = seg[k + 1];
             }
             if (s1 > s0) {
-                c.k = k; c.base = s0; c.s1 = s1; c.cnt = min(CE, s1 - s0);
-                c.idx = 0; c.grp = grp;
-                c.last = s0 + CE >= s1; c.valid = true;
+                c.k = k; c.base = s0; c.s1 = s1; c.idx = 0; c.sl = sl; c.valid = true;
                 break;
             }
         }
         return c;
     };
     auto advance = [&](const TcChunk& c) {
-        if (!c.last) {
+        if (!c.last()) {
             TcChunk n = c;
             n.base = c.base + CE;
-            n.cnt = min(CE, c.s1 - n.base);
-            n.last = n.base + CE >= c.s1;
             n.idx = c.idx + 1;
-            n.grp = (n.idx % FOLD) ? c.grp : c.grp + 1;
             return n;
         }
-        return first_of(c.k + gridDim.x, c.grp + 1);
+        return first_of(c.k + gridDim.x, c.sl + 1);
     };
 
     if (warp == TcGram::NBUILD) {
         // ------------------------------------------------------------ MMA warp
+        // The first chunk of a slice puts all three products into its hi*hi
+        // accumulator; later chunks send the cross terms to the slice's
+        // cross-term accumulator (their truncation bias is 2^-11 smaller).
         if (lane == 0) {
             constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) |
                                        ((uint32_t)(TcGram::NCOL >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
             const uint64_t desc0 = tc_sdesc(tc_smem_u32(ops));
-            // L2 prefetch of the inputs of the chunk PF_AHEAD chunks ahead
-            // (16-byte aligned ranges, clipped to the level's entries)
-            const uint64_t h_end = ((uint64_t)seg[S] * R * 8) & ~(uint64_t)15;
-            const uint64_t t_end = ((uint64_t)seg[S] * 8) & ~(uint64_t)15;
-            auto prefetch = [&](const TcChunk& c) {
-                auto range = [&](const void* base, uint64_t b0, uint64_t b1, uint64_t end) {
-                    b0 &= ~(uint64_t)15;
-                    b1 = (b1 + 15) & ~(uint64_t)15;
-                    if (b1 > end) b1 = end;
-                    if (b1 > b0)
-                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
-                                     ::"l"((const char*)base + b0), "r"((uint32_t)(b1 - b0))
-                                     : "memory");
-                };
-                range(H, (uint64_t)c.base * R * 8, (uint64_t)(c.base + c.cnt) * R * 8, h_end);
-                range(Wm, (uint64_t)c.base * R * 8, (uint64_t)(c.base + c.cnt) * R * 8, h_end);
-                range(tv, (uint64_t)c.base * 8, (uint64_t)(c.base + c.cnt) * 8, t_end);
-            };
-            TcChunk pf = first_of(blockIdx.x, 0);
-            if (PF == 0) pf.valid = false;
-            for (int i = 0; i < PF && pf.valid; ++i) {
-                prefetch(pf);
-                pf = advance(pf);
-            }
             int g = 0;
             for (TcChunk c = first_of(blockIdx.x, 0); c.valid; c = advance(c), ++g) {
-                const int b = g & 1, slot = c.grp % NSLOT;
-                if (pf.valid) {
-                    prefetch(pf);
-                    pf = advance(pf);
-                }
+                const int b = g & 1, bs = g % NBIG;
                 tc_wait(tc_smem_u32(&full[b]), (uint32_t)((g >> 1) & 1), abort_s, err);
-                const bool fresh = c.idx % FOLD == 0;   // the first chunk of a group overwrites D
-                if (fresh && c.grp >= NSLOT)
-                    tc_wait(tc_smem_u32(&accempty[slot]), (uint32_t)((c.grp / NSLOT - 1) & 1), abort_s, err);
+                if (g >= NBIG)
+                    tc_wait(tc_smem_u32(&accempty[bs]), (uint32_t)((g / NBIG - 1) & 1), abort_s, err);
+                if (c.idx == 1 && c.sl >= 1)
+                    tc_wait(tc_smem_u32(&sempty[0]), (uint32_t)((c.sl - 1) & 1), abort_s, err);
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 if (*abort_s) continue;
-                const uint32_t d_big = tmem + (uint32_t)(slot * (1 + SEP) * 128);
-                const uint32_t d_small = d_big + (SEP ? 128u : 0u);
+                const uint32_t d_big = tmem + (uint32_t)(bs * 128);
+                const uint32_t d_small = tmem + (uint32_t)TcGram::SMALL_COL;
+                const bool head = c.idx == 0;
                 const uint64_t sd = desc0 + (uint64_t)((b * TcGram::STAGE) >> 4);
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
@@ -311,24 +294,24 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
                         const uint64_t B[3] = {b_hi, b_lo, b_hi};
 #pragma unroll
                         for (int t = 0; t < 3; ++t) {
-                            // t = 2 is hi*hi; with SEP the cross terms t = 0, 1 go to d_small
-                            const bool big = SEP ? t == 2 : true;
-                            const bool first = fresh && part == 0 && ks == 0 && (SEP ? (t == 0 || t == 2) : t == 0);
-                            const uint32_t en = first ? 0u : 1u;
+                            // t = 2 is hi*hi, t = 0, 1 the cross terms
+                            const bool big = head || t == 2;
+                            const bool start = part == 0 && ks == 0 &&
+                                               (big ? t == (head ? 0 : 2) : (c.idx == 1 && t == 0));
                             asm volatile(
                                 "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(big ? d_big : d_small),
-                                "l"(A[t]), "l"(B[t]), "r"(IDESC), "r"(en));
+                                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                                ::"r"(big ? d_big : d_small), "l"(A[t]), "l"(B[t]), "r"(IDESC),
+                                "r"(start ? 0u : 1u));
                         }
                     }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              ::"r"(tc_smem_u32(&empty[b]))
                              : "memory");
-                if (c.idx % FOLD == FOLD - 1 || c.last)
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                                 ::"r"(tc_smem_u32(&accfull[slot]))
-                                 : "memory");
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(tc_smem_u32(&accfull[bs]))
+                             : "memory");
             }
             if (*abort_s && g >= 1) {
                 // let the issued MMAs drain (bounded) before the TMEM is freed
@@ -339,111 +322,131 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
         __syncwarp();
     } else {
         // ------------------------------------------------------- builder warps
-        // Kahan sums of this thread's accumulator lane and columns: warp w
-        // reads TMEM lanes 32 (w & 3) .. +31; column group cg = w >> 2 owns
-        // columns 16 cg .. 16 cg + 15 and 64 + 4 cg .. 64 + 4 cg + 3.
-        const int row = 32 * (warp & 3) + lane;
-        const int cg = warp >> 2;
-        float sum[20], comp[20];
+        // Fold layout: warp w reads TMEM lanes 32 qd .. 32 qd + 31 (qd = w & 3,
+        // rows: 0..63 -Im K, 64..127 Re K, row index p = lane row mod 64) and
+        // columns 32 hf .. 32 hf + 31 (hf = w >> 2), plus column 64 (y) when
+        // hf = 0.  Only the lower triangle q <= p is needed: quadrants 0 and
+        // 2 (p < 32) skip columns 32..63.
+        const int qd = warp & 3, hf = warp >> 2;
+        const int row = 32 * qd + lane;
+        const bool need_main = (qd & 1) || hf == 0;
+        const bool need_y = hf == 0;
+        float sum[33], comp[33];
 #pragma unroll
-        for (int j = 0; j < 20; ++j) { sum[j] = 0.f; comp[j] = 0.f; }
-        auto col_of = [&](int j) { return j < 16 ? 16 * cg + j : 64 + 4 * cg + (j - 16); };
+        for (int j = 0; j < 33; ++j) { sum[j] = 0.f; comp[j] = 0.f; }
 
-        auto fold = [&](const TcChunk& c) {
-            const int slot = c.grp % NSLOT;
-            tc_wait(tc_smem_u32(&accfull[slot]), (uint32_t)((c.grp / NSLOT) & 1), abort_s, err);
+        auto fold = [&](const TcFold& f) {
+            const int bs = f.gc % NBIG;
+            tc_wait(tc_smem_u32(&accfull[bs]), (uint32_t)((f.gc / NBIG) & 1), abort_s, err);
             __syncwarp();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            float v[20];
-            const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(slot * (1 + SEP) * 128);
-            tc_ld16(ta + 16 * cg, v);
-            tc_ld4(ta + 64 + 4 * cg, v + 16);
-            if (SEP) {
-                float w[20];
-                tc_ld16(ta + 128 + 16 * cg, w);
-                tc_ld4(ta + 128 + 64 + 4 * cg, w + 16);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
+            float v[33];
+            if (need_main) {
+                tc_ld16(lane_base + bs * 128 + 32 * hf, v);
+                tc_ld16(lane_base + bs * 128 + 32 * hf + 16, v + 16);
+            }
+            if (need_y) tc_ld1(lane_base + bs * 128 + 64, v + 32);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tc_arrive(tc_smem_u32(&accempty[bs]));
+            if (need_main) {
 #pragma unroll
-                for (int j = 0; j < 20; ++j) v[j] += w[j];
-            } else {
+                for (int j = 0; j < 32; ++j) {
+                    const float y = v[j] - comp[j];
+                    const float t = sum[j] + y;
+                    comp[j] = (t - sum[j]) - y;
+                    sum[j] = t;
+                }
+            }
+            if (need_y) {
+                const float y = v[32] - comp[32];
+                const float t = sum[32] + y;
+                comp[32] = (t - sum[32]) - y;
+                sum[32] = t;
+            }
+            if (!f.last) return;
+            // end of the slice: add the cross terms, release their accumulator
+            float w[33];
+#pragma unroll
+            for (int j = 0; j < 33; ++j) w[j] = 0.f;
+            if (f.multi) {
+                if (need_main) {
+                    tc_ld16(lane_base + TcGram::SMALL_COL + 32 * hf, w);
+                    tc_ld16(lane_base + TcGram::SMALL_COL + 32 * hf + 16, w + 16);
+                }
+                if (need_y) tc_ld1(lane_base + TcGram::SMALL_COL + 64, w + 32);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) tc_arrive(tc_smem_u32(&accempty[slot]));
+            if (lane == 0) tc_arrive(tc_smem_u32(&sempty[0]));
+            if (need_main) {
 #pragma unroll
-            for (int j = 0; j < 20; ++j) {
-                const float y = v[j] - comp[j];
-                const float t = sum[j] + y;
-                comp[j] = (t - sum[j]) - y;
-                sum[j] = t;
+                for (int j = 0; j < 32; ++j) scr[row * TcGram::SCR_LD + 32 * hf + j] = (sum[j] - comp[j]) + w[j];
             }
-            if (c.last) {
-                // corrected sums -> scratch -> coalesced record stores
+            if (need_y) scr[row * TcGram::SCR_LD + 64] = (sum[32] - comp[32]) + w[32];
 #pragma unroll
-                for (int j = 0; j < 20; ++j) {
-                    scr[row * TcGram::SCR_LD + col_of(j)] = sum[j] - comp[j];
-                    sum[j] = 0.f;
-                    comp[j] = 0.f;
-                }
-                asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
-                float2* out = rec + (size_t)c.k * (NPK + D);
-                for (int x = tid; x < NPK; x += NB) {
-                    int p = (int)((sqrtf(8.f * (float)x + 1.f) - 1.f) * 0.5f);
-                    while ((p + 1) * (p + 2) / 2 <= x) ++p;
-                    while (p * (p + 1) / 2 > x) --p;
-                    const int q = x - p * (p + 1) / 2;
-                    out[x] = make_float2(scr[(64 + p) * TcGram::SCR_LD + q], -scr[p * TcGram::SCR_LD + q]);
-                }
-                for (int p = tid; p < D; p += NB)
-                    out[NPK + p] =
-                        make_float2(scr[(64 + p) * TcGram::SCR_LD + 64], -scr[p * TcGram::SCR_LD + 64]);
-                asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
+            for (int j = 0; j < 33; ++j) { sum[j] = 0.f; comp[j] = 0.f; }
+            asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
+            // record: row p of the packed lower triangle is contiguous
+            float2* out = rec + (size_t)f.k * (NPK + D);
+            for (int p = warp; p < D; p += TcGram::NBUILD) {
+                float2* orow = out + p * (p + 1) / 2;
+                for (int q = lane; q <= p; q += 32)
+                    orow[q] = make_float2(scr[(64 + p) * TcGram::SCR_LD + q], -scr[p * TcGram::SCR_LD + q]);
+                if (lane == 0)
+                    out[NPK + p] = make_float2(scr[(64 + p) * TcGram::SCR_LD + 64], -scr[p * TcGram::SCR_LD + 64]);
             }
+            asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
         };
 
         // operand rows of this thread: entry e = lane, rows q = r8 + 8 j
-        // (j = jb .. jb + 3) with r8 = w & 7, so the swizzled offset inside a
-        // row group is fixed per thread
-        const int r8 = warp & 7, jb = 4 * (warp >> 3);
+        // (j = 0..7) with r8 = w, so the swizzled offset inside a row group
+        // is fixed per thread
+        const int r8 = warp;
         const uint32_t t_off = (uint32_t)(r8 * 128 + ((((lane >> 2) ^ r8)) << 4) + (lane & 3) * 4);
         const int e = lane;
 
         // the h_p, w_c (and t) this thread needs for chunk c, in registers
-        // (rank 8: p = j and c = r8, so one w and four consecutive h)
-        constexpr int NW = R == 8 ? 1 : 4;
-        struct Vals { float2 h[4], w[NW], t; };
+        // (rank 8: p = j and c = r8, so one w and the whole h)
+        constexpr int NW = R == 8 ? 1 : 8;
+        struct Vals { float2 h[8], w[NW], t; };
         auto load = [&](const TcChunk& c, Vals& vl) {
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) vl.h[jj] = make_float2(0.f, 0.f);
+            for (int j = 0; j < 8; ++j) vl.h[j] = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int jj = 0; jj < NW; ++jj) vl.w[jj] = make_float2(0.f, 0.f);
+            for (int j = 0; j < NW; ++j) vl.w[j] = make_float2(0.f, 0.f);
             vl.t = make_float2(0.f, 0.f);
-            if (!c.valid || e >= c.cnt) return;
+            if (!c.valid || e >= c.cnt()) return;
             const size_t ent = (size_t)(c.base + e);
             if (R == 8) {
-                const float4* hp = (const float4*)(H + ent * R + jb);
-                const float4 h01 = __ldg(hp), h23 = __ldg(hp + 1);
-                vl.h[0] = make_float2(h01.x, h01.y);
-                vl.h[1] = make_float2(h01.z, h01.w);
-                vl.h[2] = make_float2(h23.x, h23.y);
-                vl.h[3] = make_float2(h23.z, h23.w);
+                const float4* hp = (const float4*)(H + ent * R);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float4 h2 = __ldg(hp + j);
+                    vl.h[2 * j] = make_float2(h2.x, h2.y);
+                    vl.h[2 * j + 1] = make_float2(h2.z, h2.w);
+                }
                 vl.w[0] = __ldg(Wm + ent * R + r8);
             } else {
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const int q = r8 + 8 * (jb + jj);
+                for (int j = 0; j < 8; ++j) {
+                    const int q = r8 + 8 * j;
                     if (q < D) {
-                        vl.h[jj] = __ldg(H + ent * R + q / R);
-                        vl.w[jj % NW] = __ldg(Wm + ent * R + q % R);
+                        vl.h[j] = __ldg(H + ent * R + q / R);
+                        vl.w[j % NW] = __ldg(Wm + ent * R + q % R);
                     }
                 }
             }
             if (warp == 0) vl.t = __ldg(tv + ent);
         };
 
-        TcChunk cur = first_of(blockIdx.x, 0), prev;
-        prev.valid = false;
+        TcChunk cur = first_of(blockIdx.x, 0);
+        TcFold f1, f2;   // chunks g-1 and g-2, folded two chunks late
+        f1.valid = false;
+        f2.valid = false;
         Vals vc, vn;
         load(cur, vc);
         int g = 0;
@@ -465,11 +468,10 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
                 put(16 * 1024 + t_off, 1, h1, l1);
             }
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const int j = jb + jj;
+            for (int j = 0; j < 8; ++j) {
                 const int q = r8 + 8 * j;
                 if (q < D) {
-                    const float2 hv = vc.h[jj], wq = vc.w[jj % NW];
+                    const float2 hv = vc.h[j], wq = vc.w[j % NW];
                     const float u = hv.x * wq.x - hv.y * wq.y;
                     const float v = hv.x * wq.y + hv.y * wq.x;
                     uint32_t uh, ul, vh, vl;
@@ -485,13 +487,19 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) tc_arrive(tc_smem_u32(&full[b]));
-            if (prev.valid && (prev.idx % FOLD == FOLD - 1 || prev.last)) fold(prev);
-            prev = cur;
+            if (f2.valid) fold(f2);
+            f2 = f1;
+            f1.valid = true;
+            f1.k = cur.k;
+            f1.gc = g;
+            f1.last = cur.last();
+            f1.multi = cur.idx > 0;
             cur = nxt;
             vc = vn;
             ++g;
         }
-        if (prev.valid) fold(prev);   // the last chunk always ends its group
+        if (f2.valid) fold(f2);
+        if (f1.valid) fold(f1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
