@@ -170,6 +170,41 @@ def oracle_sample(prob, frac_every: int):
     return prob.i[sel], prob.j[sel], prob.t[sel]
 
 
+def run_batched(bfc_mod, count=64, max_sweeps=20, tol=1e-4):
+    """The batched workload (64 independent problems, n in 1024..16384,
+    r in {4, 6, 8}, |Omega| = c n log2 n, c in [4, 8]) in the precision form
+    through bfc_batch_complete: low-rank starts, then rounds of graph-replayed
+    sweeps on per-problem streams until each problem's training error is
+    below tol or max_sweeps ran; Gram kernel autotuned per rank."""
+    import synth
+    probs = synth.batch_problems(count)
+    cs = [bfc_mod.Completion(p.n, p.L, p.b, p.r, p.lam, p.i, p.j, p.t, p.it, p.jt, p.tt,
+                             prec=bfc_mod.PREC_C64, max_sweeps=max_sweeps, tol=tol,
+                             seed=synth.BATCH_SEED_BASE + 16 * q + synth.SEED_INIT,
+                             init_kind=1, lr_sweeps=10)
+          for q, p in enumerate(probs)]
+    try:
+        t0 = time.perf_counter()
+        last = bfc_mod.batch_complete(cs)
+        wall = time.perf_counter() - t0
+    finally:
+        for c in cs:
+            c.close()
+    sweeps = [st["sweep"] for st in last]
+    entry_sweeps = sum(p.nnz * s for p, s in zip(probs, sweeps))
+    gram = {}
+    for p, st in zip(probs, last):
+        gram[str(p.r)] = "tensor" if st["gram_impl"] == 0 else "cuda"
+    test = sorted(st["test_rel_err"] for st in last)
+    return {"workload": f"{count} problems, n in 1024..16384, r in {{4,6,8}}, |Omega| = c n log2 n, "
+                        "c in [4,8], precision form, low-rank start (10 sweeps), tol 1e-4 train",
+            "problems": count, "entries_total": int(sum(p.nnz for p in probs)),
+            "sweeps_total": int(sum(sweeps)), "seconds": wall,
+            "entry_sweeps_per_s": entry_sweeps / wall,
+            "gram_kernel_by_rank": gram,
+            "test_rel_err_median": test[len(test) // 2], "test_rel_err_max": test[-1]}
+
+
 def time_oracle_sweep(prob, X0, frac_every: int):
     import oracle
     i, j, t = oracle_sample(prob, frac_every)
@@ -367,6 +402,9 @@ def run_bfc(args, rank, world, local_rank):
             "specified_workload_best_test_rel_err": best,
             "specified_workload_note": "|Omega| = 4 n log2 n: test error does not fall below 1 (information limit)"}
 
+    if not args.no_batch and not args.n:
+        line["batched"] = run_batched(bfc)
+
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -391,6 +429,7 @@ def main():
     ap.add_argument("--prec", default="c64", choices=["c64", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance runs")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload run")
     ap.add_argument("--gram", default="tensor", choices=["tensor", "cuda"],
                     help="precision-form middle-level Gram: tcgen05 tensor cores or CUDA cores")
     ap.add_argument("--n", type=int, default=0,

@@ -116,6 +116,8 @@ typedef struct {
     int64_t refined_fallbacks; /* precision form: FP64 Cholesky fallbacks    */
     int64_t refine_steps;   /* precision form: refinement steps taken        */
     int64_t launches;       /* kernels this call launched (sweep + errors)   */
+    int32_t gram_impl;      /* middle-level Gram kernel used: 0 tensor cores,
+                               1 CUDA cores, -1 FP64 path                    */
 } bfc_sweep_stats;
 
 typedef struct {
@@ -206,6 +208,21 @@ bfc_status bfc_lowrank_init(bfc_ctx* ctx, int32_t R, int32_t sweeps,
  * records; *nsweeps (may be NULL) the number of sweeps run. */
 bfc_status bfc_complete(bfc_ctx* ctx, bfc_sweep_stats* history, int32_t history_cap,
                         int32_t* nsweeps);
+
+/* Batched form: the full workflow of bfc_complete (start, sweeps until
+ * params.tol or params.max_sweeps, FP64 refinement sweeps) for `count`
+ * independent problems, each with its own context and params.  The sweeps
+ * of all unfinished problems are enqueued round by round, each on its own
+ * context's stream as one replay of a captured CUDA graph of the sweep, so
+ * the problems run concurrently on the GPU.  In the precision form with
+ * gram_impl 0, the Gram kernel is autotuned per rank: the first problem of
+ * each rank r <= 8 runs one warm-up and one timed sweep with each kernel
+ * (ordinary sweeps, counted) and the faster serves all problems of that
+ * rank.  last (may be NULL) receives the last sweep's statistics of each
+ * problem.  A context may appear once; contexts must live on the current
+ * device.  No counterpart in the paper's listings: the batch is the
+ * independent-problem parallelism of Sec. 4 applied across problems. */
+bfc_status bfc_batch_complete(int32_t count, bfc_ctx* const* ctxs, bfc_sweep_stats* last);
 
 /* Index decoding on the GPU (Eq. (indices) and the App. A.2 slice ids):
  * for m host pairs (i[e], j[e]) writes keys[e * (L+2) + l] = i for l = 0, the

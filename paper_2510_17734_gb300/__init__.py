@@ -25,7 +25,8 @@ __all__ = [
     "bfc_num_params", "bfc_create", "bfc_set_stream", "bfc_set_factors", "bfc_get_factors",
     "bfc_eval", "bfc_als_sweep", "bfc_grad", "bfc_lowrank_init", "bfc_complete",
     "bfc_profile_enable", "bfc_profile_read", "bfc_last_error", "bfc_destroy",
-    "bfc_decode", "bfc_get_order", "bfc_residual_noalloc", "bfc_lbfgs",
+    "bfc_decode", "bfc_get_order", "bfc_residual_noalloc", "bfc_lbfgs", "bfc_batch_complete",
+    "batch_complete", "GRAM_TENSOR", "GRAM_CUDA",
 ]
 
 PREC_FP64 = 0
@@ -39,7 +40,7 @@ STATUS = {0: "BFC_OK", 1: "BFC_EINVAL", 2: "BFC_ENOMEM", 3: "BFC_ECUDA", 4: "BFC
 exported_symbols = (
     "bfc_num_params", "bfc_create", "bfc_set_stream", "bfc_set_factors", "bfc_get_factors",
     "bfc_eval", "bfc_als_sweep", "bfc_grad", "bfc_lbfgs", "bfc_lowrank_init", "bfc_complete",
-    "bfc_decode", "bfc_get_order", "bfc_residual_noalloc",
+    "bfc_batch_complete", "bfc_decode", "bfc_get_order", "bfc_residual_noalloc",
     "bfc_profile_enable", "bfc_profile_read", "bfc_last_error", "bfc_destroy",
 )
 
@@ -65,7 +66,8 @@ class SweepStats(ctypes.Structure):
                 ("test_rel_err", ctypes.c_double), ("objective", ctypes.c_double),
                 ("sweep_ms", ctypes.c_double), ("entries_per_s", ctypes.c_double),
                 ("singular_slices", ctypes.c_int64), ("refined_fallbacks", ctypes.c_int64),
-                ("refine_steps", ctypes.c_int64), ("launches", ctypes.c_int64)]
+                ("refine_steps", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("gram_impl", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -120,6 +122,8 @@ def load():
         lib.bfc_lowrank_init.restype = i32
         lib.bfc_complete.argtypes = [vp, sp, i32, ctypes.POINTER(i32)]
         lib.bfc_complete.restype = i32
+        lib.bfc_batch_complete.argtypes = [i32, ctypes.POINTER(vp), sp]
+        lib.bfc_batch_complete.restype = i32
         lib.bfc_decode.argtypes = [i64, i32, i32, i64, vp, vp, vp]
         lib.bfc_decode.restype = i32
         lib.bfc_get_order.argtypes = [vp, i32, vp, vp]
@@ -229,6 +233,21 @@ def bfc_complete(ctx, history_cap: int = 256):
     ns = ctypes.c_int32(0)
     _check(load().bfc_complete(ctx, hist, history_cap, ctypes.byref(ns)), ctx)
     return [hist[q] for q in range(min(ns.value, history_cap))]
+
+
+def bfc_batch_complete(ctxs):
+    """Batched full workflow over independent contexts; returns the last
+    sweep's statistics of each."""
+    count = len(ctxs)
+    arr = (ctypes.c_void_p * max(count, 1))(*[c for c in ctxs])
+    last = (SweepStats * max(count, 1))()
+    _check(load().bfc_batch_complete(count, arr, last), None)
+    return [last[q] for q in range(count)]
+
+
+def batch_complete(completions):
+    """bfc_batch_complete over Completion objects; returns stats dicts."""
+    return [st.as_dict() for st in bfc_batch_complete([c.ctx for c in completions])]
 
 
 def bfc_decode(n: int, L: int, b: int, i, j):

@@ -315,6 +315,9 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
     if (p.prec != BFC_PREC_FP64 && p.prec != BFC_PREC_C64_FP64SOLVE)
         return fail(nullptr, BFC_EINVAL, "unknown precision");
     if (p.gram_impl != 0 && p.gram_impl != 1) return fail(nullptr, BFC_EINVAL, "gram_impl must be 0 or 1");
+    if (p.max_sweeps < 0 || p.refine_sweeps < 0 || p.lr_sweeps < 0 || p.lr_rank < 0)
+        return fail(nullptr, BFC_EINVAL, "sweep counts and lr_rank must be >= 0");
+    if (p.init_kind != 0 && p.init_kind != 1) return fail(nullptr, BFC_EINVAL, "init_kind must be 0 or 1");
     if (in.nnz <= 0 || in.nnz >= ((int64_t)1 << 31) - 1) return fail(nullptr, BFC_EINVAL, "nnz must be in [1, 2^31-2]");
     if (in.ntest < 0 || in.ntest >= ((int64_t)1 << 31) - 1) return fail(nullptr, BFC_EINVAL, "bad ntest");
     if (!in.i || !in.j || !in.t) return fail(nullptr, BFC_EINVAL, "null training data");
@@ -388,25 +391,80 @@ static bfc_status test_error(Ctx* c, int slot)
     return BFC_OK;
 }
 
-static bfc_status sweep_impl(Ctx* c, bfc_sweep_stats* out)
+// Device work of one sweep on c->stream: kernels and memsets only, so it can
+// be captured into a graph.
+static bfc_status sweep_enqueue(Ctx* c)
 {
     const Ops* ops = get_ops(c->fp32, c->r);
-    const int64_t launched0 = c->n_launch;
     BFC_CK(c, cudaMemsetAsync(c->d_count, 0, 3 * sizeof(unsigned long long), c->stream));
-    BFC_CK(c, cudaEventRecord(c->ev0, c->stream));
     BFC_TRY(ops->sweep(c));
     BFC_TRY(factor_sumsq(c, 2));
     BFC_TRY(test_error(c, 3));
-    BFC_CK(c, cudaEventRecord(c->ev1, c->stream));
+    return BFC_OK;
+}
+
+// Wait for an enqueued sweep and read its statistics.
+static bfc_status sweep_finish(Ctx* c, bfc_sweep_stats* out, int64_t launched)
+{
     c->sweeps_done += 1;
     BFC_TRY(sync(c));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
     BFC_TRY(collect_stats(c, out, ms));
-    if (out) out->launches = c->n_launch - launched0;
+    if (out) {
+        out->launches = launched;
+        out->gram_impl = c->fp32 ? (c->gram_tc ? 0 : 1) : -1;
+    }
     return BFC_OK;
 }
 
+static bfc_status sweep_impl(Ctx* c, bfc_sweep_stats* out)
+{
+    const int64_t launched0 = c->n_launch;
+    BFC_CK(c, cudaEventRecord(c->ev0, c->stream));
+    BFC_TRY(sweep_enqueue(c));
+    BFC_CK(c, cudaEventRecord(c->ev1, c->stream));
+    return sweep_finish(c, out, c->n_launch - launched0);
+}
+
+static void drop_graph(Ctx* c)
+{
+    if (c->sweep_graph) cudaGraphExecDestroy(c->sweep_graph);
+    c->sweep_graph = nullptr;
+}
+
+// Capture one sweep of this context into a graph (once per Gram kernel
+// choice).  Leaves no graph and returns BFC_OK when the stream cannot be
+// captured (the legacy default stream); the caller then enqueues directly.
+static bfc_status capture_sweep(Ctx* c)
+{
+    if (c->sweep_graph && c->graph_tc == c->gram_tc) return BFC_OK;
+    drop_graph(c);
+    if (c->prof) return BFC_OK;   // profiling records events per kernel: no graph
+    const int64_t l0 = c->n_launch;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return BFC_OK;
+    }
+    const bfc_status st = sweep_enqueue(c);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (st != BFC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(c, BFC_ECUDA, std::string("sweep capture: ") + cudaGetErrorString(e));
+    const cudaError_t e2 = cudaGraphInstantiate(&c->sweep_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+        c->sweep_graph = nullptr;
+        return fail(c, BFC_ECUDA, std::string("sweep graph: ") + cudaGetErrorString(e2));
+    }
+    c->graph_launches = c->n_launch - l0;   // kernels recorded by the capture
+    c->n_launch = l0;                        // nothing ran yet
+    c->graph_tc = c->gram_tc;
+    return BFC_OK;
+}
 
 // Gradient of f (with lambda S when include_reg) into the device vector G;
 // hs[0] = sum |x - t|^2 over the training entries, hs[2] = ||S||^2.
@@ -754,11 +812,10 @@ static void splitmix_cnormal(uint64_t seed, uint64_t& k, int64_t count, double s
     }
 }
 
-bfc_status bfc_complete(bfc_ctx* ctx, bfc_sweep_stats* history, int32_t history_cap, int32_t* nsweeps)
+// Start of the full workflow: the optional low-rank start (init_kind 1).
+static bfc_status complete_init(Ctx* c)
 {
-    Ctx* c = (Ctx*)ctx;
-    if (!c) return BFC_EINVAL;
-    if (nsweeps) *nsweeps = 0;
+    bfc_ctx* ctx = (bfc_ctx*)c;
     if (c->P.init_kind == 1) {
         const int R = c->P.lr_rank > 0 ? c->P.lr_rank : c->r;
         if (R > c->r) return fail(c, BFC_EINVAL, "lr_rank > r");
@@ -779,6 +836,60 @@ bfc_status bfc_complete(bfc_ctx* ctx, bfc_sweep_stats* history, int32_t history_
         c->P.values_on_device = saved;
         BFC_TRY(st);
     }
+    return BFC_OK;
+}
+
+// End of the full workflow in the precision form: params.refine_sweeps
+// sweeps of the FP64 path from the current factors, in a child context on
+// the same data; the factors come back into this context.  Stats of each
+// sweep go to history[*done ...].
+static bfc_status complete_refine(Ctx* c, bfc_sweep_stats* history, int32_t history_cap, int32_t* done)
+{
+    if (!c->fp32 || c->P.refine_sweeps <= 0) return BFC_OK;
+    bfc_params fp = c->P;
+    fp.prec = BFC_PREC_FP64;
+    fp.values_on_device = 1;
+    fp.init_kind = 0;
+    fp.refine_sweeps = 0;
+    Inputs in{c->N, c->d_i, c->d_j, (const double*)c->d_t, c->NT, c->d_it, c->d_jt, (const double*)c->d_tt,
+              cudaMemcpyDeviceToDevice};
+    BFC_TRY(sync(c));
+    bfc_ctx* child = nullptr;
+    bfc_status st = create_impl(&fp, in, &child);
+    if (st != BFC_OK) return fail(c, st, std::string("FP64 refinement context: ") + g_create_err);
+    Ctx* fc = (Ctx*)child;
+    cudaError_t e = cudaMemcpyAsync(fc->z1d, c->z1d, (size_t)c->Pn * 16, cudaMemcpyDeviceToDevice, fc->stream);
+    if (e != cudaSuccess) st = fail(c, BFC_ECUDA, std::string("refinement copy: ") + cudaGetErrorString(e));
+    for (int s = 0; s < c->P.refine_sweeps && st == BFC_OK; ++s) {
+        bfc_sweep_stats rs{};
+        st = sweep_impl(fc, &rs);
+        if (st != BFC_OK) {
+            st = fail(c, st, "FP64 refinement sweep: " + fc->err);
+            break;
+        }
+        c->sweeps_done += 1;
+        rs.sweep = c->sweeps_done;
+        if (history && *done < history_cap) history[*done] = rs;
+        ++*done;
+    }
+    if (st == BFC_OK) st = sync(fc);
+    if (st == BFC_OK) {
+        e = cudaMemcpyAsync(c->z1d, fc->z1d, (size_t)c->Pn * 16, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = fail(c, BFC_ECUDA, std::string("refinement copy back: ") + cudaGetErrorString(e));
+    }
+    bfc_destroy(child);
+    BFC_TRY(st);
+    BFC_TRY(refresh_copies(c));
+    return sync(c);
+}
+
+bfc_status bfc_complete(bfc_ctx* ctx, bfc_sweep_stats* history, int32_t history_cap, int32_t* nsweeps)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    if (nsweeps) *nsweeps = 0;
+    BFC_TRY(complete_init(c));
     int done = 0;
     for (int s = 0; s < c->P.max_sweeps; ++s) {
         bfc_sweep_stats st{};
@@ -787,7 +898,102 @@ bfc_status bfc_complete(bfc_ctx* ctx, bfc_sweep_stats* history, int32_t history_
         ++done;
         if (st.train_rel_err < c->P.tol) break;
     }
+    bfc_status st = complete_refine(c, history, history_cap, &done);
     if (nsweeps) *nsweeps = done;
+    return st;
+}
+
+bfc_status bfc_batch_complete(int32_t count, bfc_ctx* const* ctxs, bfc_sweep_stats* last)
+{
+    if (count < 0 || (count > 0 && !ctxs)) return fail(nullptr, BFC_EINVAL, "bad batch arguments");
+    std::vector<Ctx*> cs((size_t)count);
+    for (int32_t q = 0; q < count; ++q) {
+        cs[q] = (Ctx*)ctxs[q];
+        if (!cs[q]) return fail(nullptr, BFC_EINVAL, "null context in the batch");
+        for (int32_t p = 0; p < q; ++p)
+            if (cs[p] == cs[q]) return fail(nullptr, BFC_EINVAL, "a context appears twice in the batch");
+    }
+    auto bad = [&](Ctx* c, bfc_status st) {
+        g_create_err = "batch: " + c->err;
+        return st;
+    };
+    std::vector<bfc_sweep_stats> st((size_t)count);
+    std::vector<int> done((size_t)count, 0);
+    std::vector<char> active((size_t)count, 1);
+    for (int32_t q = 0; q < count; ++q) {
+        const bfc_status s0 = complete_init(cs[q]);
+        if (s0 != BFC_OK) return bad(cs[q], s0);
+        if (cs[q]->P.max_sweeps <= 0) active[q] = 0;
+    }
+    auto stop = [&](int32_t q) {
+        return st[q].train_rel_err < cs[q]->P.tol || done[q] >= cs[q]->P.max_sweeps;
+    };
+    // Autotune the middle-level Gram kernel per rank in the precision form
+    // (gram_impl 0: tensor cores unless the CUDA-core kernel is faster on
+    // this batch): on the first problem of each rank, one warm-up and one
+    // timed sweep with each kernel; the faster serves every problem of that
+    // rank.  The four sweeps are ordinary ALS sweeps of that problem.
+    for (int r = 1; r <= 8; ++r) {
+        int32_t q0 = -1;
+        for (int32_t q = 0; q < count; ++q)
+            if (cs[q]->fp32 && cs[q]->r == r && cs[q]->P.gram_impl == 0 && active[q]) { q0 = q; break; }
+        if (q0 < 0 || cs[q0]->P.max_sweeps < 4) continue;
+        Ctx* c = cs[q0];
+        float ms[2] = {0.f, 0.f};
+        for (int trial = 0; trial < 4 && active[q0]; ++trial) {
+            c->gram_tc = (trial & 1) == 0;
+            const bfc_status s1 = sweep_impl(c, &st[q0]);
+            if (s1 != BFC_OK) return bad(c, s1);
+            done[q0] += 1;
+            if (trial >= 2) ms[trial & 1] = (float)st[q0].sweep_ms;
+            if (stop(q0)) active[q0] = 0;
+        }
+        const bool tc = !(ms[1] > 0.f && ms[0] > 0.f && ms[1] < ms[0]);
+        for (int32_t q = 0; q < count; ++q)
+            if (cs[q]->fp32 && cs[q]->r == r && cs[q]->P.gram_impl == 0) cs[q]->gram_tc = tc;
+    }
+    // rounds: every active problem's sweep is enqueued on its own stream
+    // (one graph launch each), then the statistics are read
+    for (int32_t q = 0; q < count; ++q)
+        if (active[q]) {
+            const bfc_status s2 = capture_sweep(cs[q]);
+            if (s2 != BFC_OK) return bad(cs[q], s2);
+        }
+    for (;;) {
+        bool any = false;
+        for (int32_t q = 0; q < count; ++q) {
+            if (!active[q]) continue;
+            any = true;
+            Ctx* c = cs[q];
+            if (cudaEventRecord(c->ev0, c->stream) != cudaSuccess) return bad(c, fail(c, BFC_ECUDA, "event"));
+            if (c->sweep_graph) {
+                if (cudaGraphLaunch(c->sweep_graph, c->stream) != cudaSuccess)
+                    return bad(c, fail(c, BFC_ECUDA, "graph launch"));
+                c->n_launch += c->graph_launches;
+            } else {
+                const bfc_status s3 = sweep_enqueue(c);
+                if (s3 != BFC_OK) return bad(c, s3);
+            }
+            if (cudaEventRecord(c->ev1, c->stream) != cudaSuccess) return bad(c, fail(c, BFC_ECUDA, "event"));
+        }
+        if (!any) break;
+        for (int32_t q = 0; q < count; ++q) {
+            if (!active[q]) continue;
+            Ctx* c = cs[q];
+            const bfc_status s4 = sweep_finish(c, &st[q], c->sweep_graph ? c->graph_launches : 0);
+            if (s4 != BFC_OK) return bad(c, s4);
+            done[q] += 1;
+            if (stop(q)) active[q] = 0;
+        }
+    }
+    for (int32_t q = 0; q < count; ++q) {
+        int32_t d = 0;
+        std::vector<bfc_sweep_stats> rs((size_t)std::max(cs[q]->P.refine_sweeps, 1));
+        const bfc_status s5 = complete_refine(cs[q], rs.data(), (int32_t)rs.size(), &d);
+        if (s5 != BFC_OK) return bad(cs[q], s5);
+        if (d > 0) st[q] = rs[d - 1];   // the last FP64 refinement sweep
+        if (last) last[q] = st[q];
+    }
     return BFC_OK;
 }
 
@@ -866,6 +1072,7 @@ void bfc_destroy(bfc_ctx* ctx)
     if (!c) return;
     if (c->own_stream) cudaStreamSynchronize(c->own_stream);
     if (c->stream && c->stream != c->own_stream) cudaStreamSynchronize(c->stream);
+    drop_graph(c);
     for (void* p : c->allocs) cudaFree(p);
     for (auto& p : c->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);

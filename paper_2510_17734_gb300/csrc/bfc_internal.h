@@ -82,6 +82,10 @@ struct Ctx {
     // sweep bookkeeping
     int32_t sweeps_done = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // one captured sweep (kernels and memsets only), replayed by the batch
+    cudaGraphExec_t sweep_graph = nullptr;
+    int64_t graph_launches = 0;     // kernels in the captured sweep
+    bool graph_tc = false;          // Gram kernel the capture used
 
     // profiling
     bool prof = false;
