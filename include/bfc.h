@@ -68,9 +68,10 @@ typedef enum {
     /* Everything in FP64: environment chains, normal-equation sums, solves. */
     BFC_PREC_FP64 = 0,
     /* Precision form: chains and normal-equation sums in complex64 with
-     * compensated accumulation; per-slice solves and the factor master copy
-     * in FP64 (complex64 Cholesky with FP64 iterative refinement, FP64
-     * Cholesky fallback). */
+     * compensated accumulation (tensor cores for r <= 8, see gram_impl);
+     * per-slice solves refined to FP64-level accuracy (complex64 Cholesky,
+     * iterative refinement with a double-float residual and solution, FP64
+     * Cholesky fallback); factor master copy in FP64. */
     BFC_PREC_C64_FP64SOLVE = 1
 } bfc_precision;
 

@@ -296,7 +296,7 @@ static bfc_status build(Ctx* c, const Inputs& in)
     BFC_TRY(dalloc(c, &c->rec, ops->record_bytes(n, S), "normal-equation records"));
     const size_t fbb = ops->fallback_bytes(S);
     if (fbb > 0 && L > 0) {
-        BFC_TRY(dalloc(c, (void**)&c->fb, fbb, "FP64 refinement records"));
+        BFC_TRY(dalloc(c, (void**)&c->fb, fbb, "FP64 fallback records"));
         BFC_TRY(dalloc(c, (void**)&c->fblist, (size_t)S * sizeof(int32_t), "fallback list"));
     }
     BFC_TRY(ops->configure(c));

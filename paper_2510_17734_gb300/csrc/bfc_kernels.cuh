@@ -845,12 +845,13 @@ template <typename T, int R> struct SolveCfg {
 
 // Middle level m, stage 2 (solve + left update): one warp per slice.
 // Precision form (float): complex64 Cholesky of the Jacobi-equilibrated
-// S (K + lambda I) S, complex64 solve, then up to three steps of FP64
-// iterative refinement (residual y - (K + lambda I) s in FP64 with rows spread
-// over the lanes, correction through the complex64 factor);
-// if the factorization breaks down or the refinement does not contract, the
-// system is solved by an FP64 Cholesky instead (counted in nref).  FP64 path
-// (double): FP64 Cholesky directly.  The slice is written row-major in FP64
+// S (K + lambda I) S, complex64 solve, then up to three steps of iterative
+// refinement: the residual y - (K + lambda I) s is formed in double-float
+// arithmetic (TwoSum-compensated float pairs, rows spread over the lanes)
+// against a solution kept as a double-float pair, and the correction goes
+// through the complex64 factor.  If the factorization breaks down or the
+// refinement does not contract, the slice goes on a list for the FP64
+// Cholesky of k_mid_fallback.  FP64 path (double): FP64 Cholesky directly.  The slice is written row-major in FP64
 // and the compute type; then h_{m+1}(e) = h_m(e)^T Z^{m+1}(k) for the slice's
 // entries is scattered into order m+1.  A singular system keeps its old slice.
 template <typename T, int R>
@@ -862,7 +863,7 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
             unsigned long long* __restrict__ nsing, unsigned long long* __restrict__ nfb,
             unsigned long long* __restrict__ nsteps, int32_t* __restrict__ fblist, int S)
 {
-    // nfb: slices handed to the FP64 fallback (length of fblist); nsteps: FP64 refinement steps
+    // nfb: slices handed to the FP64 fallback (length of fblist); nsteps: refinement steps
     typedef typename cvec<T>::type V;
     typedef SolveCfg<T, R> C;
     constexpr int D = C::D, NPK = C::NPK, NS = C::NS;
