@@ -353,8 +353,16 @@ def run_bfc(args, rank, world, local_rank):
         # the nominal dense TF32 / BF16 ratio 1.1 / 2.25
         peak_tflops = peaks.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25
         executed = prob.nnz * TC_FLOPS_PER_ENTRY / (mid_avg_ms * 1e-3) / 1e12
+        # DRAM bytes per launch from the ncu capture summarised in
+        # profiles/k_mid_gram_tc_n32768_c64.md (n = 32768, scaled to this
+        # workload by training entries for reads and slices for writes)
+        traffic = None
+        if not args.n:
+            traffic = 242.374656e6 * prob.nnz / 1769472 + 52.970752e6 * 2
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tflops, "traffic": None,
+                    "frac": achieved / peak_tflops, "traffic": traffic,
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at "
+                                      "n=32768, scaled by entries (reads) and slices (writes)",
                     "kernel": "k_mid_gram_tc (tcgen05 per-slice normal equations, one launch per middle level)",
                     "launch_ms": mid_avg_ms, "flop_per_launch": flops_per_launch,
                     "peak_source": "MEASURED_PEAKS bf16_tflops_sustained x 1.1/2.25 (of measured)",

@@ -99,11 +99,14 @@ __device__ __forceinline__ void tc_split(float x, uint32_t& hi, uint32_t& lo)
     lo = (__float_as_uint(r) + 0x1000u) & 0xFFFFE000u;
 }
 
+// One potentially blocking test of an mbarrier phase: the thread may be
+// suspended for up to 1 microsecond while the phase is incomplete, instead of
+// spinning on issue slots the other warps need.
 __device__ __forceinline__ bool tc_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
         : "r"(bar), "r"(parity)
         : "memory");
