@@ -225,6 +225,79 @@ bfc_status bfc_complete(bfc_ctx* ctx, bfc_sweep_stats* history, int32_t history_
  * independent-problem parallelism of Sec. 4 applied across problems. */
 bfc_status bfc_batch_complete(int32_t count, bfc_ctx* const* ctxs, bfc_sweep_stats* last);
 
+/* Gauge fixing (left orthogonalization).  Eq. (BF_tensor_rep) is unchanged
+ * when an invertible r x r matrix is inserted on a bond between two factors
+ * (the network's gauge freedom).  Level by level from S^1, every bond group
+ * is factored M = Q R, with R upper triangular with a real positive
+ * diagonal (unique), and replaced by Q; R moves into the next factor.  The
+ * groups are: the b x r leaf blocks of z1; then, for each middle level and
+ * bond, the two slices sharing it, stacked 2r x r.  Every factor but zL
+ * ends left-orthonormal; zL carries the norm.  The FP64 factors are
+ * updated in place (entries are unchanged to rounding).  Needs b >= r.
+ * The paper has no counterpart: used to give the learned start consistent
+ * training targets. */
+bfc_status bfc_canonicalize(bfc_ctx* ctx);
+
+/* ---- Learned initializer (a small MLP from problem parameters to factors) */
+
+/* Opaque model: in -> hidden -> hidden -> out with GELU after both hidden
+ * layers and a linear output; FP32 master weights with Adam state, BF16
+ * weights in every forward / backward kernel, FP32 activations and
+ * accumulation.  Inputs are mapped to [-1, 1] by stored ranges; the network
+ * predicts per-output standardized values (stored mean and standard
+ * deviation).  The model owns its device memory; one model per host thread.
+ * The paper has no counterpart: this is the learned replacement of the
+ * low-rank start of Sec. 4.2. */
+typedef struct bfc_mlp bfc_mlp;
+
+/* He-normal weights from SplitMix64(seed), zero biases, identity scaling.
+ * 1 <= in_dim <= 64, 1 <= hidden <= 256, 1 <= out_dim <= 2^31. */
+bfc_status bfc_mlp_create(int32_t in_dim, int32_t hidden, int64_t out_dim, uint64_t seed, bfc_mlp** out);
+
+/* Sizes (any pointer may be NULL); parameter count of the flat layout
+ * [W1 (in x hidden) | b1 | W2 (hidden x hidden) | b2 | W3 (hidden x out) |
+ * b3], each W input-major (W[k][n] at k * fan_out + n). */
+void bfc_mlp_dims(const bfc_mlp* m, int32_t* in_dim, int32_t* hidden, int64_t* out_dim);
+int64_t bfc_mlp_num_params(const bfc_mlp* m);
+
+/* Flat FP32 master parameters as host doubles (get) or from host doubles
+ * (set; the BF16 copy is refreshed). */
+bfc_status bfc_mlp_get_params(bfc_mlp* m, double* params);
+bfc_status bfc_mlp_set_params(bfc_mlp* m, const double* params);
+
+/* Input ranges [lo, hi] (in_dim each, hi > lo) and output mean / standard
+ * deviation (out_dim each, std > 0), host arrays. */
+bfc_status bfc_mlp_set_scaling(bfc_mlp* m, const double* in_lo, const double* in_hi,
+                               const double* out_mean, const double* out_std);
+
+/* Predictions y[s * out_dim + q] (de-standardized) for `count` host inputs
+ * x[s * in_dim + q]. */
+bfc_status bfc_mlp_forward(bfc_mlp* m, int32_t count, const double* x, double* y);
+
+/* Mean squared error of the standardized prediction against the
+ * standardized targets of 1 <= count <= 32 samples, and its gradient with
+ * respect to the flat parameters (grads may be NULL; loss may be NULL). */
+bfc_status bfc_mlp_grad(bfc_mlp* m, int32_t count, const double* x, const double* y,
+                        double* grads, double* loss);
+
+/* Training on `count` samples: sets the input ranges and output scaling from
+ * the data, then `epochs` passes of Adam (lr, beta 0.9 / 0.999) over shuffled
+ * mini-batches of `batch` (1..32) samples (SplitMix64(seed) order).
+ * loss_history (may be NULL) receives the mean batch loss of each epoch. */
+bfc_status bfc_mlp_train(bfc_mlp* m, int32_t count, const double* x, const double* y, int32_t epochs,
+                         int32_t batch, double lr, uint64_t seed, double* loss_history);
+
+void bfc_mlp_destroy(bfc_mlp* m);
+
+/* Learned start: the model's prediction for the inputs (omega / (pi n),
+ * offset) becomes the context's factors (model output size must be 2 P).
+ * With allow_fallback, the low-rank start of bfc_complete's init_kind 1 is
+ * also computed and whichever has the lower training error (Eq.
+ * (BF_convergence)) is kept.  *used_learned (may be NULL) tells which;
+ * *start_err (may be NULL) receives the kept start's training error. */
+bfc_status bfc_init_learned(bfc_ctx* ctx, bfc_mlp* model, double omega, double offset,
+                            int32_t allow_fallback, int32_t* used_learned, double* start_err);
+
 /* Index decoding on the GPU (Eq. (indices) and the App. A.2 slice ids):
  * for m host pairs (i[e], j[e]) writes keys[e * (L+2) + l] = i for l = 0, the
  * slice id k_{l+1} of S^{l+1} for l = 1..L, and j for l = L+1.  These are

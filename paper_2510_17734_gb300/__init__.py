@@ -27,6 +27,9 @@ __all__ = [
     "bfc_profile_enable", "bfc_profile_read", "bfc_last_error", "bfc_destroy",
     "bfc_decode", "bfc_get_order", "bfc_residual_noalloc", "bfc_lbfgs", "bfc_batch_complete",
     "batch_complete", "GRAM_TENSOR", "GRAM_CUDA",
+    "bfc_mlp_create", "bfc_mlp_dims", "bfc_mlp_num_params", "bfc_mlp_get_params", "bfc_mlp_set_params",
+    "bfc_mlp_set_scaling", "bfc_mlp_forward", "bfc_mlp_grad", "bfc_mlp_train", "bfc_mlp_destroy",
+    "bfc_init_learned", "bfc_canonicalize", "Mlp",
 ]
 
 PREC_FP64 = 0
@@ -41,6 +44,9 @@ exported_symbols = (
     "bfc_num_params", "bfc_create", "bfc_set_stream", "bfc_set_factors", "bfc_get_factors",
     "bfc_eval", "bfc_als_sweep", "bfc_grad", "bfc_lbfgs", "bfc_lowrank_init", "bfc_complete",
     "bfc_batch_complete", "bfc_decode", "bfc_get_order", "bfc_residual_noalloc",
+    "bfc_mlp_create", "bfc_mlp_dims", "bfc_mlp_num_params", "bfc_mlp_get_params", "bfc_mlp_set_params",
+    "bfc_mlp_set_scaling", "bfc_mlp_forward", "bfc_mlp_grad", "bfc_mlp_train", "bfc_mlp_destroy",
+    "bfc_init_learned", "bfc_canonicalize",
     "bfc_profile_enable", "bfc_profile_read", "bfc_last_error", "bfc_destroy",
 )
 
@@ -124,6 +130,31 @@ def load():
         lib.bfc_complete.restype = i32
         lib.bfc_batch_complete.argtypes = [i32, ctypes.POINTER(vp), sp]
         lib.bfc_batch_complete.restype = i32
+        u64 = ctypes.c_uint64
+        lib.bfc_mlp_create.argtypes = [i32, i32, i64, u64, ctypes.POINTER(vp)]
+        lib.bfc_mlp_create.restype = i32
+        lib.bfc_mlp_dims.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64)]
+        lib.bfc_mlp_dims.restype = None
+        lib.bfc_mlp_num_params.argtypes = [vp]
+        lib.bfc_mlp_num_params.restype = i64
+        lib.bfc_mlp_get_params.argtypes = [vp, vp]
+        lib.bfc_mlp_get_params.restype = i32
+        lib.bfc_mlp_set_params.argtypes = [vp, vp]
+        lib.bfc_mlp_set_params.restype = i32
+        lib.bfc_mlp_set_scaling.argtypes = [vp, vp, vp, vp, vp]
+        lib.bfc_mlp_set_scaling.restype = i32
+        lib.bfc_mlp_forward.argtypes = [vp, i32, vp, vp]
+        lib.bfc_mlp_forward.restype = i32
+        lib.bfc_mlp_grad.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(dbl)]
+        lib.bfc_mlp_grad.restype = i32
+        lib.bfc_mlp_train.argtypes = [vp, i32, vp, vp, i32, i32, dbl, u64, vp]
+        lib.bfc_mlp_train.restype = i32
+        lib.bfc_mlp_destroy.argtypes = [vp]
+        lib.bfc_mlp_destroy.restype = None
+        lib.bfc_init_learned.argtypes = [vp, vp, dbl, dbl, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
+        lib.bfc_init_learned.restype = i32
+        lib.bfc_canonicalize.argtypes = [vp]
+        lib.bfc_canonicalize.restype = i32
         lib.bfc_decode.argtypes = [i64, i32, i32, i64, vp, vp, vp]
         lib.bfc_decode.restype = i32
         lib.bfc_get_order.argtypes = [vp, i32, vp, vp]
@@ -245,6 +276,105 @@ def bfc_batch_complete(ctxs):
     return [last[q] for q in range(count)]
 
 
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def bfc_mlp_create(in_dim: int, hidden: int, out_dim: int, seed: int = 0):
+    out = ctypes.c_void_p()
+    _check(load().bfc_mlp_create(in_dim, hidden, out_dim, seed, ctypes.byref(out)), None)
+    return out.value
+
+
+def bfc_mlp_dims(m):
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    load().bfc_mlp_dims(m, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return a.value, b.value, c.value
+
+
+def bfc_mlp_num_params(m) -> int:
+    return int(load().bfc_mlp_num_params(m))
+
+
+def bfc_mlp_get_params(m):
+    out = np.zeros(bfc_mlp_num_params(m), dtype=np.float64)
+    _check(load().bfc_mlp_get_params(m, _ptr(out)), None)
+    return out
+
+
+def bfc_mlp_set_params(m, params):
+    params = _f64(params)
+    _check(load().bfc_mlp_set_params(m, _ptr(params)), None)
+
+
+def bfc_mlp_set_scaling(m, in_lo, in_hi, out_mean, out_std):
+    a, b, c, d = _f64(in_lo), _f64(in_hi), _f64(out_mean), _f64(out_std)
+    _check(load().bfc_mlp_set_scaling(m, _ptr(a), _ptr(b), _ptr(c), _ptr(d)), None)
+
+
+def bfc_mlp_forward(m, x):
+    x = _f64(x)
+    _, _, out_dim = bfc_mlp_dims(m)
+    y = np.zeros((x.shape[0], out_dim), dtype=np.float64)
+    _check(load().bfc_mlp_forward(m, x.shape[0], _ptr(x), _ptr(y)), None)
+    return y
+
+
+def bfc_mlp_grad(m, x, y):
+    x, y = _f64(x), _f64(y)
+    g = np.zeros(bfc_mlp_num_params(m), dtype=np.float64)
+    loss = ctypes.c_double(0.0)
+    _check(load().bfc_mlp_grad(m, x.shape[0], _ptr(x), _ptr(y), _ptr(g), ctypes.byref(loss)), None)
+    return g, float(loss.value)
+
+
+def bfc_mlp_train(m, x, y, epochs: int, batch: int = 32, lr: float = 1e-3, seed: int = 0):
+    x, y = _f64(x), _f64(y)
+    hist = np.zeros(max(epochs, 1), dtype=np.float64)
+    _check(load().bfc_mlp_train(m, x.shape[0], _ptr(x), _ptr(y), epochs, batch, lr, seed, _ptr(hist)), None)
+    return hist[:epochs]
+
+
+def bfc_mlp_destroy(m):
+    load().bfc_mlp_destroy(m)
+
+
+def bfc_canonicalize(ctx):
+    _check(load().bfc_canonicalize(ctx), ctx)
+
+
+def bfc_init_learned(ctx, m, omega: float, offset: float, allow_fallback: bool = True):
+    used = ctypes.c_int32(0)
+    err = ctypes.c_double(0.0)
+    _check(load().bfc_init_learned(ctx, m, omega, offset, int(allow_fallback), ctypes.byref(used),
+                                   ctypes.byref(err)), ctx)
+    return bool(used.value), float(err.value)
+
+
+class Mlp:
+    """Owner of a bfc_mlp handle (closes on exit)."""
+
+    def __init__(self, in_dim, hidden, out_dim, seed=0):
+        self.h = bfc_mlp_create(in_dim, hidden, out_dim, seed)
+
+    def close(self):
+        if self.h:
+            bfc_mlp_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def batch_complete(completions):
     """bfc_batch_complete over Completion objects; returns stats dicts."""
     return [st.as_dict() for st in bfc_batch_complete([c.ctx for c in completions])]
@@ -345,6 +475,9 @@ class Completion:
         N = int(self._nnz)
         K = self.n if level in (0, self.L + 1) else (1 << (self.L + 1))
         return bfc_get_order(self.ctx, level, N, K)
+
+    def canonicalize(self):
+        bfc_canonicalize(self.ctx)
 
     def complete(self, history_cap=256):
         return [h.as_dict() for h in bfc_complete(self.ctx, history_cap)]

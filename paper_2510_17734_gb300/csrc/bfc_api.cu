@@ -839,6 +839,22 @@ static bfc_status complete_init(Ctx* c)
     return BFC_OK;
 }
 
+// Relative error ||x - t|| / ||t|| of the current factors over the training
+// entries (Eq. (BF_convergence)), through d_scalars[12..13].
+static bfc_status train_rel_err(Ctx* c, double* err)
+{
+    const Ops* ops = get_ops(c->fp32, c->r);
+    const int nb = (int)std::min<int64_t>(1216, (c->N + 255) / 256);
+    BFC_TRY(ops->eval(c, c->d_i, c->d_j, c->N, nullptr, c->d_t, c->d_red, nb));
+    launch_reduce_pairs(c->d_red, nb, c->d_scalars + 12, c->stream);
+    BFC_LAUNCH_CHECK(c, "reduce");
+    double hs[2];
+    BFC_CK(c, cudaMemcpyAsync(hs, c->d_scalars + 12, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    BFC_TRY(sync(c));
+    *err = hs[1] > 0 ? sqrt(hs[0] / hs[1]) : sqrt(hs[0]);
+    return BFC_OK;
+}
+
 // End of the full workflow in the precision form: params.refine_sweeps
 // sweeps of the FP64 path from the current factors, in a child context on
 // the same data; the factors come back into this context.  Stats of each
@@ -901,6 +917,63 @@ bfc_status bfc_complete(bfc_ctx* ctx, bfc_sweep_stats* history, int32_t history_
     bfc_status st = complete_refine(c, history, history_cap, &done);
     if (nsweeps) *nsweeps = done;
     return st;
+}
+
+bfc_status bfc_canonicalize(bfc_ctx* ctx)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    if ((c->L > 0 && c->b < c->r) || c->n < c->r)
+        return fail(c, BFC_EINVAL, "the gauge is fixed by QR of b x r leaf blocks: needs b >= r");
+    const cudaError_t e = launch_canonicalize(c->z1d, c->Zd, c->zLd, c->n, c->L, c->b, c->r, c->stream);
+    if (e != cudaSuccess) return fail(c, BFC_ECUDA, std::string("canonicalize: ") + cudaGetErrorString(e));
+    BFC_TRY(refresh_copies(c));
+    return sync(c);
+}
+
+bfc_status bfc_init_learned(bfc_ctx* ctx, bfc_mlp* model, double omega, double offset, int32_t allow_fallback,
+                            int32_t* used_learned, double* start_err)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    if (used_learned) *used_learned = 0;
+    if (!model) return fail(c, BFC_EINVAL, "null model");
+    int32_t din = 0, dhid = 0;
+    int64_t dout = 0;
+    bfc_mlp_dims(model, &din, &dhid, &dout);
+    if (din != 2 || dout != 2 * c->Pn)
+        return fail(c, BFC_EINVAL, "model must map 2 inputs to the 2 P reals of this context's factors");
+    if (!isfinite(omega) || !isfinite(offset)) return fail(c, BFC_EINVAL, "omega and offset must be finite");
+    const double x[2] = {omega / (M_PI * (double)c->n), offset};
+    std::vector<double> y((size_t)dout);
+    bfc_status st = bfc_mlp_forward(model, 1, x, y.data());
+    if (st != BFC_OK) return fail(c, st, std::string("learned start: ") + bfc_last_error(nullptr));
+    for (double v : y)
+        if (!isfinite(v)) return fail(c, BFC_ENONFINITE, "learned start is not finite");
+    BFC_CK(c, cudaMemcpyAsync(c->z1d, y.data(), (size_t)c->Pn * 16, cudaMemcpyHostToDevice, c->stream));
+    BFC_TRY(refresh_copies(c));
+    double e_learned = 0.0;
+    BFC_TRY(train_rel_err(c, &e_learned));
+    if (used_learned) *used_learned = 1;
+    if (start_err) *start_err = e_learned;
+    if (!allow_fallback) return BFC_OK;
+    // the low-rank start remains the fallback: keep whichever fits the
+    // training entries better
+    const bfc_params saved = c->P;
+    c->P.init_kind = 1;
+    st = complete_init(c);
+    c->P = saved;
+    BFC_TRY(st);
+    double e_lr = 0.0;
+    BFC_TRY(train_rel_err(c, &e_lr));
+    if (e_lr < e_learned) {
+        if (used_learned) *used_learned = 0;
+        if (start_err) *start_err = e_lr;
+        return BFC_OK;
+    }
+    BFC_CK(c, cudaMemcpyAsync(c->z1d, y.data(), (size_t)c->Pn * 16, cudaMemcpyHostToDevice, c->stream));
+    BFC_TRY(refresh_copies(c));
+    return sync(c);
 }
 
 bfc_status bfc_batch_complete(int32_t count, bfc_ctx* const* ctxs, bfc_sweep_stats* last)

@@ -43,4 +43,8 @@ void launch_axpy(double* y, const double* x, double alpha, int64_t n, cudaStream
 void launch_embed(const double2* A, const double2* B, int64_t n, int R, int r, int64_t nslices, double2* z1,
                   double2* Z, double2* zL, cudaStream_t st);
 
+// Left-orthogonal gauge of the FP64 factors (bfc_gauge.cu).
+cudaError_t launch_canonicalize(double2* z1, double2* Z, double2* zL, int64_t n, int L, int b, int r,
+                                cudaStream_t st);
+
 }  // namespace bfc

@@ -381,3 +381,82 @@ def test_lbfgs_monotone_and_reaches_stationarity():
     g, f = oracle.grad(n, L, b, r, lam, X, i, j, t)
     assert abs(f - hist[-1]) <= 1e-12 * abs(f)
     assert np.linalg.norm(g) < 1e-3 * np.linalg.norm(g0)
+
+
+# ----------------------------------------------------------- MLP oracle
+
+def test_bf16_rounding_is_nearest_even():
+    from oracle import mlp
+    u = 2.0 ** -7   # bfloat16 spacing on [1, 2)
+    vals = [1.0, 3.0, 1 + u / 2, 1 + 3 * u / 2, 1 + u / 2 + 2.0 ** -20, -(1 + 3 * u / 2), 0.0]
+    want = [1.0, 3.0, 1.0, 1 + 2 * u, 1 + u, -(1 + 2 * u), 0.0]
+    np.testing.assert_array_equal(mlp.bf16_round(np.array(vals)), np.array(want))
+
+
+def test_gelu_closed_forms():
+    from oracle import mlp
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0
+    assert abs(mlp.gelu_grad(np.array([0.0]))[0] - 0.5) < 1e-15
+    assert abs(mlp.gelu(np.array([10.0]))[0] - 10.0) < 1e-12
+    assert abs(mlp.gelu(np.array([-10.0]))[0]) < 1e-12
+    a = np.linspace(-4, 4, 17)
+    hstep = 1e-6
+    fd = (mlp.gelu(a + hstep) - mlp.gelu(a - hstep)) / (2 * hstep)
+    np.testing.assert_allclose(mlp.gelu_grad(a), fd, rtol=1e-7, atol=1e-9)
+
+
+def test_mlp_backprop_matches_finite_differences():
+    from oracle import mlp
+    dims = (2, 5, 7)
+    _, npar = mlp.layout(*dims)
+    rng = np.random.default_rng(3)
+    p = rng.normal(size=npar) * 0.5
+    x = rng.uniform(-1, 1, size=(4, 2))
+    t = rng.normal(size=(4, 7))
+    loss, g = mlp.loss_and_grad(p, dims, x, t, bf16=False)
+    assert abs(loss - np.mean((mlp.forward(p, dims, x, bf16=False) - t) ** 2)) < 1e-14
+    fd = np.zeros(npar)
+    hstep = 1e-6
+    for q in range(npar):
+        e = np.zeros(npar)
+        e[q] = hstep
+        fd[q] = (mlp.loss_and_grad(p + e, dims, x, t, bf16=False)[0]
+                 - mlp.loss_and_grad(p - e, dims, x, t, bf16=False)[0]) / (2 * hstep)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9)
+
+
+# ----------------------------------------------------------- gauge oracle
+
+def _random_factors(n, L, r, seed):
+    rng = np.random.default_rng(seed)
+    P = oracle.num_params(n, L, n >> L, r)
+    return rng.normal(size=P) + 1j * rng.normal(size=P)
+
+
+@pytest.mark.parametrize("n,L,b,r", [(64, 3, 8, 3), (96, 4, 6, 2), (40, 0, 40, 4)])
+def test_canonical_gauge_keeps_entries_and_is_orthonormal_and_unique(n, L, b, r):
+    from oracle import gauge
+    X = _random_factors(n, L, r, 7)
+    C = gauge.canonicalize(n, L, b, r, X)
+    rng = np.random.default_rng(8)
+    i = rng.integers(0, n, 300).astype(np.int32)
+    j = rng.integers(0, n, 300).astype(np.int32)
+    xa = oracle.eval_entries(n, L, b, r, X, i, j)
+    xc = oracle.eval_entries(n, L, b, r, C, i, j)
+    assert np.max(np.abs(xa - xc)) <= 1e-11 * np.max(np.abs(xa))
+    # left-orthonormal: each leaf block of z1 and each stacked slice pair
+    z1 = C[:n * r].reshape(n, r)
+    if L > 0:
+        for p in range(n // b):
+            blk = z1[p * b:(p + 1) * b]
+            np.testing.assert_allclose(blk.conj().T @ blk, np.eye(r), atol=1e-12)
+        S = 1 << (L + 1)
+        Z = C[n * r:n * r + L * S * r * r].reshape(L, S, r, r)
+        for m in range(1, L + 1):
+            for A in range(1 << (L - m)):
+                for B in range(1 << m):
+                    M = np.vstack([Z[m - 1, ((A << 1) << m) | B], Z[m - 1, ((A << 1 | 1) << m) | B]])
+                    np.testing.assert_allclose(M.conj().T @ M, np.eye(r), atol=1e-12)
+    # a second application changes nothing (the gauge is fixed)
+    C2 = gauge.canonicalize(n, L, b, r, C)
+    assert np.max(np.abs(C2 - C)) <= 1e-11 * np.max(np.abs(C))
