@@ -205,6 +205,114 @@ def run_batched(bfc_mod, count=64, max_sweeps=20, tol=1e-4):
             "test_rel_err_median": test[len(test) // 2], "test_rel_err_max": test[-1]}
 
 
+def run_learned(bfc_mod, n_train=64, n_test=8, epochs=200, max_sweeps=30, tol=1e-3, c_obs=36, with_nn=False):
+    """The learned-start workload: family n = 4096, L = 8, b = 16, r = 6,
+    omega / (pi n) ~ U[1/16, 1/4], h ~ U[0.5, 2], |Omega| = c_obs n log2 n
+    at the same sample positions for every member, lambda = 1e-7 (c_obs = 36
+    is the paper's 6 r n log n rule; 6 n log n leaves the family
+    information-limited: no held-out draw falls below test error 1).  Training:
+    n_train precision-form completions (fixed-seed low-rank start, 15 sweeps,
+    run as batches through bfc_batch_complete), gauge-fixed by
+    bfc_canonicalize, then the MLP 2 -> 256 -> 256 -> 2P trained by
+    bfc_mlp_train.  Held-out draws: ALS from the learned start (precision
+    form) against the low-rank start in the precision form and in plain
+    FP64, up to max_sweeps sweeps or test error < tol."""
+    import synth
+    n, L, b, r = 4096, 8, 16, 6
+    nobs = c_obs * n * 12
+    base = synth.BATCH_SEED_BASE + 0x10000
+    rng = synth.SplitMix64(base + synth.SEED_PARAMS)
+
+    def problem(q):
+        u = rng.uniform(2)
+        om, h = 1 / 16 + u[0] * (1 / 4 - 1 / 16), 0.5 + 1.5 * u[1]
+        return om, h, synth.make_problem(f"learned{q}", n, L, b, r, om * math.pi * n, h, nobs, 1e-7, 15, base)
+
+    def completion(p, prec, **kw):
+        return bfc_mod.Completion(p.n, p.L, p.b, p.r, p.lam, p.i, p.j, p.t, p.it, p.jt, p.tt, prec=prec, **kw)
+
+    t0 = time.perf_counter()
+    X, Y = [], []
+    for c0 in range(0, n_train, 32):
+        group = [problem(c0 + q) for q in range(min(32, n_train - c0))]
+        cs = [completion(p, bfc_mod.PREC_C64, init_kind=1, seed=777, max_sweeps=15, tol=1e-12, lr_sweeps=10)
+              for _, _, p in group]
+        try:
+            bfc_mod.batch_complete(cs)
+            for (om, h, _), c in zip(group, cs):
+                c.canonicalize()
+                X.append((om, h))
+                Y.append(c.get_factors().view(np.float64).copy())
+        finally:
+            for c in cs:
+                c.close()
+    t_data = time.perf_counter() - t0
+    X, Y = np.array(X), np.array(Y)
+    t0 = time.perf_counter()
+    model = bfc_mod.Mlp(2, 256, Y.shape[1], seed=5)
+    hist = bfc_mod.bfc_mlp_train(model.h, X, Y, epochs=epochs, batch=32, lr=1e-3, seed=3)
+    t_train = time.perf_counter() - t0
+    if not with_nn:
+        del Y
+
+    def run(p, start, prec):
+        c = completion(p, prec, init_kind=1 if start == "lowrank" else 0, seed=777, max_sweeps=0, lr_sweeps=10)
+        try:
+            t1 = time.perf_counter()
+            if start == "learned":
+                bfc_mod.bfc_init_learned(c.ctx, model.h, p.omega, p.h, allow_fallback=False)
+            elif start == "nearest":
+                om = p.omega / (math.pi * n)
+                k = int(np.argmin(((X[:, 0] - om) / 0.1875) ** 2 + ((X[:, 1] - p.h) / 1.5) ** 2))
+                c.set_factors(Y[k].view(np.complex128))
+            else:
+                c.complete()
+            errs, reached = [], None
+            for s in range(max_sweeps):
+                st = c.sweep()
+                errs.append(st["test_rel_err"])
+                if st["test_rel_err"] < tol:
+                    reached = time.perf_counter() - t1
+                    break
+            return errs, reached
+        finally:
+            c.close()
+
+    out = {"learned_pc64": [], "lowrank_pc64": [], "lowrank_fp64": [], "nearest_pc64": []}
+    for q in range(n_test):
+        _, _, p = problem(10000 + q)
+        out["learned_pc64"].append(run(p, "learned", bfc_mod.PREC_C64))
+        if with_nn:
+            out["nearest_pc64"].append(run(p, "nearest", bfc_mod.PREC_C64))
+        out["lowrank_pc64"].append(run(p, "lowrank", bfc_mod.PREC_C64))
+        out["lowrank_fp64"].append(run(p, "lowrank", bfc_mod.PREC_FP64))
+    model.close()
+
+    def summary(rs):
+        e1 = [e[0] for e, _ in rs]
+        e5 = [e[min(4, len(e) - 1)] for e, _ in rs]
+        last = [e[-1] for e, _ in rs]
+        t = [x for _, x in rs if x is not None]
+        return {"test_err_after_1_sweep_median": float(np.median(e1)),
+                "test_err_after_5_sweeps_median": float(np.median(e5)),
+                "best_test_err_median": float(np.median([min(e) for e, _ in rs])),
+                "final_test_err_median": float(np.median(last)),
+                "reached_tol": f"{len(t)}/{len(rs)}",
+                "seconds_to_tol_median": float(np.median(t)) if t else None}
+
+    res = {"workload": f"n=4096 L=8 b=16 r=6 family, omega/(pi n) in [1/16,1/4], h in [0.5,2], "
+                        f"|Omega|={c_obs} n log2 n (shared positions); {n_train} training completions, "
+                        f"{n_test} held-out draws, tol {tol} test error, <= {max_sweeps} sweeps",
+            "training_data_seconds": t_data, "mlp_train_seconds": t_train,
+            "mlp_loss_first_last": [float(hist[0]), float(hist[-1])],
+            "learned_start_precision_form": summary(out["learned_pc64"]),
+            "lowrank_start_precision_form": summary(out["lowrank_pc64"]),
+            "lowrank_start_plain_fp64": summary(out["lowrank_fp64"])}
+    if with_nn:
+        res["nearest_training_completion_start"] = summary(out["nearest_pc64"])
+    return res
+
+
 def time_oracle_sweep(prob, X0, frac_every: int):
     import oracle
     i, j, t = oracle_sample(prob, frac_every)
@@ -412,6 +520,8 @@ def run_bfc(args, rank, world, local_rank):
 
     if not args.no_batch and not args.n:
         line["batched"] = run_batched(bfc)
+    if not args.no_learned and not args.n:
+        line["learned_start"] = run_learned(bfc)
 
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -438,6 +548,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance runs")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload run")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-start run")
     ap.add_argument("--gram", default="tensor", choices=["tensor", "cuda"],
                     help="precision-form middle-level Gram: tcgen05 tensor cores or CUDA cores")
     ap.add_argument("--n", type=int, default=0,
