@@ -159,6 +159,31 @@ __device__ __forceinline__ void tc_ld4(uint32_t taddr, float* v)
     for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Packed pairs of FP32 values (the f32x2 arithmetic of sm_100 and later):
+// one instruction adds or subtracts two lanes' worth of values.
+__device__ __forceinline__ uint64_t f2pack(float a, float b)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(uint64_t r, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t f2add(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2sub(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 struct TcChunk {
     int k, base, s1;   // slice id, first entry of the chunk, end of the slice
     int idx;           // chunk index within the slice
@@ -334,9 +359,11 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
         const int row = 32 * qd + lane;
         const bool need_main = (qd & 1) || hf == 0;
         const bool need_y = hf == 0;
-        float sum[33], comp[33];
+        // Kahan sums: 16 packed pairs for the 32 main columns, one scalar for y
+        uint64_t sum2[16], comp2[16];
+        float sum_y = 0.f, comp_y = 0.f;
 #pragma unroll
-        for (int j = 0; j < 33; ++j) { sum[j] = 0.f; comp[j] = 0.f; }
+        for (int j = 0; j < 16; ++j) { sum2[j] = 0ull; comp2[j] = 0ull; }
 
         auto fold = [&](const TcFold& f) {
             const int bs = f.gc % NBIG;
@@ -356,18 +383,18 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             if (lane == 0) tc_arrive(tc_smem_u32(&accempty[bs]));
             if (need_main) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float y = v[j] - comp[j];
-                    const float t = sum[j] + y;
-                    comp[j] = (t - sum[j]) - y;
-                    sum[j] = t;
+                for (int j = 0; j < 16; ++j) {
+                    const uint64_t y = f2sub(f2pack(v[2 * j], v[2 * j + 1]), comp2[j]);
+                    const uint64_t t = f2add(sum2[j], y);
+                    comp2[j] = f2sub(f2sub(t, sum2[j]), y);
+                    sum2[j] = t;
                 }
             }
             if (need_y) {
-                const float y = v[32] - comp[32];
-                const float t = sum[32] + y;
-                comp[32] = (t - sum[32]) - y;
-                sum[32] = t;
+                const float y = v[32] - comp_y;
+                const float t = sum_y + y;
+                comp_y = (t - sum_y) - y;
+                sum_y = t;
             }
             if (!f.last) return;
             // end of the slice: add the cross terms, release their accumulator
@@ -387,11 +414,19 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             if (lane == 0) tc_arrive(tc_smem_u32(&sempty[0]));
             if (need_main) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) scr[row * TcGram::SCR_LD + 32 * hf + j] = (sum[j] - comp[j]) + w[j];
+                for (int j = 0; j < 16; ++j) {
+                    float s0, s1, c0, c1;
+                    f2unpack(sum2[j], s0, s1);
+                    f2unpack(comp2[j], c0, c1);
+                    scr[row * TcGram::SCR_LD + 32 * hf + 2 * j] = (s0 - c0) + w[2 * j];
+                    scr[row * TcGram::SCR_LD + 32 * hf + 2 * j + 1] = (s1 - c1) + w[2 * j + 1];
+                }
             }
-            if (need_y) scr[row * TcGram::SCR_LD + 64] = (sum[32] - comp[32]) + w[32];
+            if (need_y) scr[row * TcGram::SCR_LD + 64] = (sum_y - comp_y) + w[32];
 #pragma unroll
-            for (int j = 0; j < 33; ++j) { sum[j] = 0.f; comp[j] = 0.f; }
+            for (int j = 0; j < 16; ++j) { sum2[j] = 0ull; comp2[j] = 0ull; }
+            sum_y = 0.f;
+            comp_y = 0.f;
             asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
             // record: row p of the packed lower triangle is contiguous
             float2* out = rec + (size_t)f.k * (NPK + D);
