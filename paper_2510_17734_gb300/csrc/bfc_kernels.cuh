@@ -809,17 +809,28 @@ __device__ __forceinline__ void slice_h_update(const typename cvec<T>::type* __r
                                                typename cvec<T>::type* __restrict__ Hn, int s0, int s1, int lane)
 {
     typedef typename cvec<T>::type V;
-    for (int p = s0 + lane; p < s1; p += 32) {
-        V h[R];
+    // two entries per lane and step: both loads are in flight together
+    for (int p = s0 + lane; p < s1; p += 64) {
+        const int p2 = p + 32;
+        const bool two = p2 < s1;
+        V h[R], g[R];
 #pragma unroll
         for (int a = 0; a < R; ++a) h[a] = H[(size_t)p * R + a];
+#pragma unroll
+        for (int a = 0; a < R; ++a) g[a] = two ? H[(size_t)p2 * R + a] : czero<V>();
         const size_t o = (size_t)nxt[p] * R;
+        const size_t o2 = two ? (size_t)nxt[p2] * R : 0;
 #pragma unroll
         for (int c = 0; c < R; ++c) {
-            V acc2 = czero<V>();
+            V acc2 = czero<V>(), acc3 = czero<V>();
 #pragma unroll
-            for (int a = 0; a < R; ++a) cmac(acc2, h[a], zt_s[a * R + c]);
+            for (int a = 0; a < R; ++a) {
+                const V z = zt_s[a * R + c];
+                cmac(acc2, h[a], z);
+                cmac(acc3, g[a], z);
+            }
             Hn[o + c] = acc2;
+            if (two) Hn[o2 + c] = acc3;
         }
     }
 }
