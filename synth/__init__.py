@@ -180,10 +180,11 @@ def config(index: int, n_override: int | None = None) -> Problem:
 
 
 def batch_problems(count: int = 64, seed_base: int = BATCH_SEED_BASE,
-                   n_choices=(1024, 2048, 4096, 8192, 16384)) -> list[Problem]:
+                   n_choices=(1024, 2048, 4096, 8192, 16384), paper_rule: bool = False) -> list[Problem]:
     """The batched workload: independent problems with n drawn from
     `n_choices` (b = 16), r uniform in {4, 6, 8}, omega ~ U[pi n/16, pi n/4],
-    receiver offset h ~ U[0.5, 2], |Omega| = c n log2 n with c ~ U[4, 8]."""
+    receiver offset h ~ U[0.5, 2], |Omega| = c n log2 n with c ~ U[4, 8]
+    (or, with paper_rule, the paper's 6 r n log2 n)."""
     out = []
     for p in range(count):
         rng = SplitMix64(seed_base + 16 * p + SEED_PARAMS)
@@ -194,7 +195,7 @@ def batch_problems(count: int = 64, seed_base: int = BATCH_SEED_BASE,
         h = 0.5 + 1.5 * u[3]
         c = 4.0 + 4.0 * u[4]
         L = int(round(math.log2(n // 16)))
-        n_obs = int(round(c * n * math.log2(n)))
+        n_obs = int(round((6 * r if paper_rule else c) * n * math.log2(n)))
         out.append(make_problem(f"batch{p}", n, L, 16, r, omega, h, n_obs, 1e-7, 20,
                                 seed_base + 16 * p))
     return out
