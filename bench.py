@@ -505,6 +505,7 @@ def run_bfc(args, rank, world, local_rank):
     flops_per_launch = prob.nnz * als_flops_per_entry(prob.r)
     clocks = clk.summary()
     peaks = load_peaks()
+    fp32_meas, fp64_meas = bfc.bfc_measure_alu_peaks()
     achieved = flops_per_launch / (mid_avg_ms * 1e-3) / 1e12
     tensor_gram = prec == bfc.PREC_C64 and args.gram == "tensor" and prob.r <= 8
     if tensor_gram:
@@ -531,13 +532,14 @@ def run_bfc(args, rank, world, local_rank):
                                      "(Re and Im, full square, 2 contraction positions per entry) x 3 TF32 "
                                      "split products = 122880 flop per entry"}
     else:
-        sm_max = peaks.get("sm_max_mhz", 2070.0)
-        peak_tflops = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        fp64_path = prec != bfc.PREC_C64
+        peak_tflops = fp64_meas if fp64_path else fp32_meas
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / peak_tflops, "traffic": None,
                     "kernel": "k_mid_gram (per-slice normal equations, one launch per middle level)",
                     "launch_ms": mid_avg_ms, "flop_per_launch": flops_per_launch,
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+                    "peak_source": ("measured FP64" if fp64_path else "measured FP32") +
+                                   " FMA-chain peak (bfc_measure_alu_peaks, of measured)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -551,6 +553,8 @@ def run_bfc(args, rank, world, local_rank):
             "gpu_launches": launches,
             "kernels_ms": {k: round(v[1] / max(args.steps, 1), 4) for k, v in prof.items()},
             "roofline": roofline,
+            "alu_peaks_measured": {"fp32_tflops": fp32_meas, "fp64_tflops": fp64_meas,
+                                   "how": "bfc_measure_alu_peaks: dependent FMA chains on all SMs, best of 5"},
             "clocks": clocks,
             "sweep_stats": {"train_rel_err": stats[-1]["train_rel_err"],
                             "test_rel_err": stats[-1]["test_rel_err"]}}

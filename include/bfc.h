@@ -298,6 +298,12 @@ void bfc_mlp_destroy(bfc_mlp* m);
 bfc_status bfc_init_learned(bfc_ctx* ctx, bfc_mlp* model, double omega, double offset,
                             int32_t allow_fallback, int32_t* used_learned, double* start_err);
 
+/* Measured FP32 and FP64 FMA throughput of the current device in TFLOP/s
+ * (dependent-FMA chains, all SMs, best of five launches; about one second).
+ * The denominators of the CUDA-core kernels' ALU rooflines.  No counterpart
+ * in the paper. */
+bfc_status bfc_measure_alu_peaks(double* fp32_tflops, double* fp64_tflops);
+
 /* Index decoding on the GPU (Eq. (indices) and the App. A.2 slice ids):
  * for m host pairs (i[e], j[e]) writes keys[e * (L+2) + l] = i for l = 0, the
  * slice id k_{l+1} of S^{l+1} for l = 1..L, and j for l = L+1.  These are

@@ -29,7 +29,7 @@ __all__ = [
     "batch_complete", "GRAM_TENSOR", "GRAM_CUDA",
     "bfc_mlp_create", "bfc_mlp_dims", "bfc_mlp_num_params", "bfc_mlp_get_params", "bfc_mlp_set_params",
     "bfc_mlp_set_scaling", "bfc_mlp_forward", "bfc_mlp_grad", "bfc_mlp_train", "bfc_mlp_destroy",
-    "bfc_init_learned", "bfc_canonicalize", "Mlp",
+    "bfc_init_learned", "bfc_canonicalize", "Mlp", "bfc_measure_alu_peaks",
 ]
 
 PREC_FP64 = 0
@@ -46,7 +46,7 @@ exported_symbols = (
     "bfc_batch_complete", "bfc_decode", "bfc_get_order", "bfc_residual_noalloc",
     "bfc_mlp_create", "bfc_mlp_dims", "bfc_mlp_num_params", "bfc_mlp_get_params", "bfc_mlp_set_params",
     "bfc_mlp_set_scaling", "bfc_mlp_forward", "bfc_mlp_grad", "bfc_mlp_train", "bfc_mlp_destroy",
-    "bfc_init_learned", "bfc_canonicalize",
+    "bfc_init_learned", "bfc_canonicalize", "bfc_measure_alu_peaks",
     "bfc_profile_enable", "bfc_profile_read", "bfc_last_error", "bfc_destroy",
 )
 
@@ -155,6 +155,8 @@ def load():
         lib.bfc_init_learned.restype = i32
         lib.bfc_canonicalize.argtypes = [vp]
         lib.bfc_canonicalize.restype = i32
+        lib.bfc_measure_alu_peaks.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+        lib.bfc_measure_alu_peaks.restype = i32
         lib.bfc_decode.argtypes = [i64, i32, i32, i64, vp, vp, vp]
         lib.bfc_decode.restype = i32
         lib.bfc_get_order.argtypes = [vp, i32, vp, vp]
@@ -337,6 +339,12 @@ def bfc_mlp_train(m, x, y, epochs: int, batch: int = 32, lr: float = 1e-3, seed:
 
 def bfc_mlp_destroy(m):
     load().bfc_mlp_destroy(m)
+
+
+def bfc_measure_alu_peaks():
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().bfc_measure_alu_peaks(ctypes.byref(a), ctypes.byref(b)), None)
+    return float(a.value), float(b.value)
 
 
 def bfc_canonicalize(ctx):

@@ -377,3 +377,10 @@ def test_lbfgs_parity(cfg2s, prec):
     else:
         # complex64 gradients: the trajectory agrees to the gradient precision
         np.testing.assert_allclose(fg, fo, rtol=1e-3)
+
+
+def test_measured_alu_peaks_are_plausible():
+    f32, f64 = bfc.bfc_measure_alu_peaks()
+    # FMA-chain rates on a full GPU: tens of TFLOP/s in FP32, FP64 far below it
+    assert 5.0 < f32 < 500.0
+    assert 0.05 < f64 < f32 / 4
