@@ -212,10 +212,11 @@ bfc_status bfc_complete(bfc_ctx* ctx, bfc_sweep_stats* history, int32_t history_
 
 /* Batched form: the full workflow of bfc_complete (start, sweeps until
  * params.tol or params.max_sweeps, FP64 refinement sweeps) for `count`
- * independent problems, each with its own context and params.  The sweeps
- * of all unfinished problems are enqueued round by round, each on its own
- * context's stream as one replay of a captured CUDA graph of the sweep, so
- * the problems run concurrently on the GPU.  In the precision form with
+ * independent problems, each with its own context and params.  Each
+ * problem's sweep is captured once as a CUDA graph; every round launches
+ * one graph whose child graphs are the sweeps of all unfinished problems
+ * (rebuilt only when that set changes), so the problems run concurrently
+ * on the GPU from a single launch per round.  In the precision form with
  * gram_impl 0, the Gram kernel is autotuned per rank: the first problem of
  * each rank r <= 8 runs one warm-up and one timed sweep with each kernel
  * (ordinary sweeps, counted) and the faster serves all problems of that

@@ -430,7 +430,9 @@ static bfc_status sweep_impl(Ctx* c, bfc_sweep_stats* out)
 static void drop_graph(Ctx* c)
 {
     if (c->sweep_graph) cudaGraphExecDestroy(c->sweep_graph);
+    if (c->sweep_graph_src) cudaGraphDestroy(c->sweep_graph_src);
     c->sweep_graph = nullptr;
+    c->sweep_graph_src = nullptr;
 }
 
 // Capture one sweep of this context into a graph (once per Gram kernel
@@ -455,11 +457,12 @@ static bfc_status capture_sweep(Ctx* c)
     }
     if (e != cudaSuccess) return fail(c, BFC_ECUDA, std::string("sweep capture: ") + cudaGetErrorString(e));
     const cudaError_t e2 = cudaGraphInstantiate(&c->sweep_graph, g, 0);
-    cudaGraphDestroy(g);
     if (e2 != cudaSuccess) {
+        cudaGraphDestroy(g);
         c->sweep_graph = nullptr;
         return fail(c, BFC_ECUDA, std::string("sweep graph: ") + cudaGetErrorString(e2));
     }
+    c->sweep_graph_src = g;   // kept: the batch embeds it in one graph per round
     c->graph_launches = c->n_launch - l0;   // kernels recorded by the capture
     c->n_launch = l0;                        // nothing ran yet
     c->graph_tc = c->gram_tc;
@@ -1025,40 +1028,93 @@ bfc_status bfc_batch_complete(int32_t count, bfc_ctx* const* ctxs, bfc_sweep_sta
         for (int32_t q = 0; q < count; ++q)
             if (cs[q]->fp32 && cs[q]->r == r && cs[q]->P.gram_impl == 0) cs[q]->gram_tc = tc;
     }
-    // rounds: every active problem's sweep is enqueued on its own stream
-    // (one graph launch each), then the statistics are read
+    // rounds: the sweeps of all active problems are the child graphs of one
+    // graph, launched once per round (the problems run concurrently); the
+    // graph is rebuilt only when the set of active problems changes.  A
+    // problem without a captured sweep (profiling on) runs on its own stream.
     for (int32_t q = 0; q < count; ++q)
         if (active[q]) {
             const bfc_status s2 = capture_sweep(cs[q]);
             if (s2 != BFC_OK) return bad(cs[q], s2);
         }
+    cudaStream_t bs = nullptr;
+    cudaGraphExec_t round = nullptr;
+    std::vector<char> round_set;
+    auto cleanup = [&](void) {
+        if (round) cudaGraphExecDestroy(round);
+        if (bs) cudaStreamDestroy(bs);
+        round = nullptr;
+        bs = nullptr;
+    };
+    if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(nullptr, BFC_ECUDA, "batch stream");
     for (;;) {
-        bool any = false;
-        for (int32_t q = 0; q < count; ++q) {
-            if (!active[q]) continue;
-            any = true;
-            Ctx* c = cs[q];
-            if (cudaEventRecord(c->ev0, c->stream) != cudaSuccess) return bad(c, fail(c, BFC_ECUDA, "event"));
-            if (c->sweep_graph) {
-                if (cudaGraphLaunch(c->sweep_graph, c->stream) != cudaSuccess)
-                    return bad(c, fail(c, BFC_ECUDA, "graph launch"));
-                c->n_launch += c->graph_launches;
-            } else {
-                const bfc_status s3 = sweep_enqueue(c);
-                if (s3 != BFC_OK) return bad(c, s3);
+        bool any = false, all_graphs = true;
+        for (int32_t q = 0; q < count; ++q)
+            if (active[q]) {
+                any = true;
+                all_graphs = all_graphs && cs[q]->sweep_graph_src != nullptr;
             }
-            if (cudaEventRecord(c->ev1, c->stream) != cudaSuccess) return bad(c, fail(c, BFC_ECUDA, "event"));
-        }
         if (!any) break;
+        if (all_graphs) {
+            std::vector<char> want(active.begin(), active.end());
+            if (!round || want != round_set) {
+                if (round) cudaGraphExecDestroy(round);
+                round = nullptr;
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaGraphCreate(&g, 0);
+                for (int32_t q = 0; q < count && e == cudaSuccess; ++q) {
+                    if (!active[q]) continue;
+                    Ctx* c = cs[q];
+                    cudaGraphNode_t n0 = nullptr, nc = nullptr, n1 = nullptr;
+                    e = cudaGraphAddEventRecordNode(&n0, g, nullptr, 0, c->ev0);
+                    if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&nc, g, &n0, 1, c->sweep_graph_src);
+                    if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n1, g, &nc, 1, c->ev1);
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&round, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (e != cudaSuccess) {
+                    cleanup();
+                    return fail(nullptr, BFC_ECUDA, std::string("batch round graph: ") + cudaGetErrorString(e));
+                }
+                round_set = want;
+            }
+            cudaError_t e = cudaGraphLaunch(round, bs);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(bs);
+            if (e != cudaSuccess) {
+                cleanup();
+                return fail(nullptr, BFC_ECUDA, std::string("batch round: ") + cudaGetErrorString(e));
+            }
+            for (int32_t q = 0; q < count; ++q)
+                if (active[q]) cs[q]->n_launch += cs[q]->graph_launches;
+        } else {
+            for (int32_t q = 0; q < count; ++q) {
+                if (!active[q]) continue;
+                Ctx* c = cs[q];
+                if (cudaEventRecord(c->ev0, c->stream) != cudaSuccess) {
+                    cleanup();
+                    return bad(c, fail(c, BFC_ECUDA, "event"));
+                }
+                const bfc_status s3 = sweep_enqueue(c);
+                if (s3 != BFC_OK || cudaEventRecord(c->ev1, c->stream) != cudaSuccess) {
+                    cleanup();
+                    return bad(c, s3 != BFC_OK ? s3 : fail(c, BFC_ECUDA, "event"));
+                }
+            }
+        }
         for (int32_t q = 0; q < count; ++q) {
             if (!active[q]) continue;
             Ctx* c = cs[q];
             const bfc_status s4 = sweep_finish(c, &st[q], c->sweep_graph ? c->graph_launches : 0);
-            if (s4 != BFC_OK) return bad(c, s4);
+            if (s4 != BFC_OK) {
+                cleanup();
+                return bad(c, s4);
+            }
             done[q] += 1;
             if (stop(q)) active[q] = 0;
         }
     }
+    cleanup();
     for (int32_t q = 0; q < count; ++q) {
         int32_t d = 0;
         std::vector<bfc_sweep_stats> rs((size_t)std::max(cs[q]->P.refine_sweeps, 1));

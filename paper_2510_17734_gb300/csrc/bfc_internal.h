@@ -84,6 +84,7 @@ struct Ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // one captured sweep (kernels and memsets only), replayed by the batch
     cudaGraphExec_t sweep_graph = nullptr;
+    cudaGraph_t sweep_graph_src = nullptr;
     int64_t graph_launches = 0;     // kernels in the captured sweep
     bool graph_tc = false;          // Gram kernel the capture used
 
