@@ -94,14 +94,19 @@ __host__ __device__ __forceinline__ constexpr int tri(int p, int q) { return (p 
 // Right environments, one level: w_{m-1} = Z^{m+1}(k) w_m for every entry of
 // slice k (Alg. 1: the right vector v, built from the right end).  One CTA
 // per slice; the slice is staged in shared memory and read by broadcast.
+// (8 CTAs of 128 threads per SM: the slice stays in shared memory instead of
+// being hoisted into registers, so enough loads are in flight to cover DRAM
+// latency; rows of an even number of complex64 values move as 16-byte
+// vectors.)
 template <typename T, int R>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 8)
 k_env_right(const typename cvec<T>::type* __restrict__ Win,
             typename cvec<T>::type* __restrict__ Wout,
             const typename cvec<T>::type* __restrict__ Zm,
             const int32_t* __restrict__ seg, const int32_t* __restrict__ prv, int S)
 {
     typedef typename cvec<T>::type V;
+    constexpr bool VEC = sizeof(V) == 8 && R % 2 == 0;
     __shared__ V z[R * R];
     for (int k = blockIdx.x; k < S; k += gridDim.x) {
         const int s0 = seg[k], s1 = seg[k + 1];
@@ -111,15 +116,35 @@ k_env_right(const typename cvec<T>::type* __restrict__ Win,
         __syncthreads();
         for (int p = s0 + threadIdx.x; p < s1; p += blockDim.x) {
             V w[R];
+            if constexpr (VEC) {
+                const float4* src = reinterpret_cast<const float4*>(Win + (size_t)p * R);
 #pragma unroll
-            for (int c = 0; c < R; ++c) w[c] = Win[(size_t)p * R + c];
+                for (int c = 0; c < R / 2; ++c) {
+                    const float4 v = __ldg(src + c);
+                    w[2 * c].x = v.x; w[2 * c].y = v.y;
+                    w[2 * c + 1].x = v.z; w[2 * c + 1].y = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < R; ++c) w[c] = Win[(size_t)p * R + c];
+            }
             const size_t o = (size_t)prv[p] * R;
+            V res[R];
 #pragma unroll
             for (int a = 0; a < R; ++a) {
                 V acc = czero<V>();
 #pragma unroll
                 for (int c = 0; c < R; ++c) cmac(acc, z[a * R + c], w[c]);
-                Wout[o + a] = acc;
+                res[a] = acc;
+            }
+            if constexpr (VEC) {
+                float4* dst = reinterpret_cast<float4*>(Wout + o);
+#pragma unroll
+                for (int a = 0; a < R / 2; ++a)
+                    dst[a] = make_float4(res[2 * a].x, res[2 * a].y, res[2 * a + 1].x, res[2 * a + 1].y);
+            } else {
+#pragma unroll
+                for (int a = 0; a < R; ++a) Wout[o + a] = res[a];
             }
         }
     }
