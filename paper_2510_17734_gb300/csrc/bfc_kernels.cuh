@@ -834,17 +834,44 @@ __device__ __forceinline__ void slice_h_update(const typename cvec<T>::type* __r
                                                typename cvec<T>::type* __restrict__ Hn, int s0, int s1, int lane)
 {
     typedef typename cvec<T>::type V;
+    constexpr bool VEC = sizeof(V) == 8 && R % 2 == 0;   // rows as 16-byte vectors
+    auto load_row = [&](int p, V* h) {
+        if constexpr (VEC) {
+            const float4* src = reinterpret_cast<const float4*>(H + (size_t)p * R);
+#pragma unroll
+            for (int a = 0; a < R / 2; ++a) {
+                const float4 v = __ldg(src + a);
+                h[2 * a].x = v.x; h[2 * a].y = v.y;
+                h[2 * a + 1].x = v.z; h[2 * a + 1].y = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < R; ++a) h[a] = H[(size_t)p * R + a];
+        }
+    };
+    auto store_row = [&](size_t o, const V* x) {
+        if constexpr (VEC) {
+            float4* dst = reinterpret_cast<float4*>(Hn + o);
+#pragma unroll
+            for (int a = 0; a < R / 2; ++a) dst[a] = make_float4(x[2 * a].x, x[2 * a].y, x[2 * a + 1].x, x[2 * a + 1].y);
+        } else {
+#pragma unroll
+            for (int a = 0; a < R; ++a) Hn[o + a] = x[a];
+        }
+    };
     // two entries per lane and step: both loads are in flight together
     for (int p = s0 + lane; p < s1; p += 64) {
         const int p2 = p + 32;
         const bool two = p2 < s1;
         V h[R], g[R];
+        load_row(p, h);
+        if (two) load_row(p2, g);
+        else
 #pragma unroll
-        for (int a = 0; a < R; ++a) h[a] = H[(size_t)p * R + a];
-#pragma unroll
-        for (int a = 0; a < R; ++a) g[a] = two ? H[(size_t)p2 * R + a] : czero<V>();
+            for (int a = 0; a < R; ++a) g[a] = czero<V>();
         const size_t o = (size_t)nxt[p] * R;
         const size_t o2 = two ? (size_t)nxt[p2] * R : 0;
+        V r1[R], r2[R];
 #pragma unroll
         for (int c = 0; c < R; ++c) {
             V acc2 = czero<V>(), acc3 = czero<V>();
@@ -854,9 +881,11 @@ __device__ __forceinline__ void slice_h_update(const typename cvec<T>::type* __r
                 cmac(acc2, h[a], z);
                 cmac(acc3, g[a], z);
             }
-            Hn[o + c] = acc2;
-            if (two) Hn[o2 + c] = acc3;
+            r1[c] = acc2;
+            r2[c] = acc3;
         }
+        store_row(o, r1);
+        if (two) store_row(o2, r2);
     }
 }
 
