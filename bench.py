@@ -46,8 +46,6 @@ METRIC = "ALS sweep entries/s (n=65536 precision form)"
 UNIT = "entries/s"
 WORKLOAD = ("n=65536 L=12 b=16 r=8, exp(i w rho)/rho line-to-line kernel, w=pi n/16, h=1.5, "
             "|Omega|=4 n log2 n (3774874 train / 419430 test), lambda=1e-7")
-FP32_LANES_PER_SM = 128
-NUM_SMS = 152
 TC_FLOPS_PER_ENTRY = 2 * 3 * 128 * 80 * 2   # flop, 2 positions x M 128 x N 80 x 3 products
 
 
