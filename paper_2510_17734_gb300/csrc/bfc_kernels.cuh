@@ -1014,29 +1014,40 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
                         if (p < D) s_df[p] = make_float4(sh[s].x, sh[s].y, sl[s].x, sl[s].y);
                     }
                     __syncwarp();
+                    // one pass over q for all rows of the lane: s_q is read once
+                    // for them, and K_pq comes from the stored lower triangle
+                    // (conjugated above the diagonal), so no lane idles
+                    float4 acc[NS];
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
+                        const int p = lane + 32 * s;
+                        acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (p < D) {
+                            const V yp = K[NPK + p];
+                            acc[s] = make_float4(yp.x, 0.f, yp.y, 0.f);
+                            df_sub_cmul(acc[s], make_float2(lamf, 0.f), sh[s], sl[s]);
+                        }
+                    }
+#pragma unroll 2
+                    for (int q = 0; q < D; ++q) {
+                        const float4 sq = s_df[q];
+#pragma unroll
+                        for (int s = 0; s < NS; ++s) {
+                            const int p = lane + 32 * s;
+                            if (p < D) {
+                                const bool lo = q <= p;
+                                const V kv = K[lo ? tri(p, q) : tri(q, p)];
+                                df_sub_cmul(acc[s], make_float2(kv.x, lo ? kv.y : -kv.y), make_float2(sq.x, sq.y),
+                                            make_float2(sq.z, sq.w));
+                            }
+                        }
+                    }
                     float rr[NS][2];
                     float rmax = 0.f;
 #pragma unroll
                     for (int s = 0; s < NS; ++s) {
-                        const int p = lane + 32 * s;
-                        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (p < D) {
-                            const V yp = K[NPK + p];
-                            acc = make_float4(yp.x, 0.f, yp.y, 0.f);
-                            df_sub_cmul(acc, make_float2(lamf, 0.f), sh[s], sl[s]);
-                            for (int q = 0; q <= p; ++q) {   // K_pq s_q
-                                const float4 sq = s_df[q];
-                                df_sub_cmul(acc, K[tri(p, q)], make_float2(sq.x, sq.y), make_float2(sq.z, sq.w));
-                            }
-                            for (int q = p + 1; q < D; ++q) {  // conj(K_qp) s_q
-                                const float4 sq = s_df[q];
-                                const V kq = K[tri(q, p)];
-                                df_sub_cmul(acc, make_float2(kq.x, -kq.y), make_float2(sq.x, sq.y),
-                                            make_float2(sq.z, sq.w));
-                            }
-                        }
-                        rr[s][0] = acc.x + acc.y;
-                        rr[s][1] = acc.z + acc.w;
+                        rr[s][0] = acc[s].x + acc[s].y;
+                        rr[s][1] = acc[s].z + acc[s].w;
                         rmax = fmaxf(rmax, fmaxf(fabsf(rr[s][0]), fabsf(rr[s][1])));
                     }
 #pragma unroll
