@@ -125,6 +125,71 @@ def als_flops_per_entry(r: int) -> int:
     return 8 * (r * r * (r * r + 1) // 2 + r * r)
 
 
+def kernel_rooflines(prob, prof, stats, peaks, fp32_meas, main_roof):
+    """Per-kernel algorithmic work against the measured peaks (complex64
+    precision form), from the library's CUDA-event timers of the timed sweeps.
+
+    Bytes are what the algorithm must move through HBM per launch (complex64
+    values of 8 bytes, 4-byte indices), flops are 8 per complex multiply-add
+    of the algorithm's own operation count.  `frac` is against the measured
+    copy bandwidth for the streaming kernels and the measured FP32 FMA peak
+    for arithmetic."""
+    n, L, r, nnz = prob.n, prob.L, prob.r, prob.nnz
+    S = 1 << (L + 1)
+    D = r * r
+    npk = D * (D + 1) // 2
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    slices = L * S * max(len(stats), 1)
+    steps_avg = sum(int(st["refine_steps"]) for st in stats) / slices
+
+    def avg_ms(key):
+        cnt, tot = prof.get(key, (0, 0.0))
+        return tot / cnt if cnt else None
+
+    out = []
+    ms = avg_ms("env_right")
+    if ms:
+        by = nnz * (16 * r + 4) + S * D * 8
+        a = by / (ms * 1e-3) / 1e9
+        out.append({"kernel": "k_env_right", "bound": "hbm", "launch_ms": ms, "bytes": by,
+                    "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                    "per_unit": f"{16 * r + 4} B per entry (w in, w out, level map) + {D * 8} B per slice"})
+    ms = avg_ms("mid_gram")
+    if ms:
+        fl = nnz * als_flops_per_entry(r)
+        a = fl / (ms * 1e-3) / 1e12
+        out.append({"kernel": main_roof["kernel"].split(" ")[0], "bound": main_roof["bound"],
+                    "launch_ms": ms, "flop": fl, "achieved": a, "unit": "TFLOP/s",
+                    "peak": main_roof["peak"], "frac": main_roof["frac"],
+                    "fp32_peak": fp32_meas, "fp32_frac": a / fp32_meas,
+                    "per_unit": f"{als_flops_per_entry(r)} flop per entry (Hermitian Gram + right-hand side)",
+                    "note": "fp32_frac: the same complex64-accurate contraction against the measured "
+                            "FP32 FMA peak of the CUDA cores"})
+    ms = avg_ms("mid_solve")
+    if ms:
+        by = S * (npk + D) * 8 + nnz * (16 * r + 4) + S * D * 24 + 4 * (S + 1)
+        fl = S * (4.0 / 3.0 * D ** 3 + 8.0 * D * D * (2 * (1 + steps_avg) + steps_avg)) + nnz * 8 * D
+        a = by / (ms * 1e-3) / 1e9
+        af = fl / (ms * 1e-3) / 1e12
+        out.append({"kernel": "k_mid_solve", "bound": "hbm", "launch_ms": ms, "bytes": by,
+                    "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                    "flop": fl, "fp32_achieved_tflops": af, "fp32_peak": fp32_meas, "fp32_frac": af / fp32_meas,
+                    "refine_steps_per_slice": steps_avg,
+                    "per_unit": f"{(npk + D) * 8 + D * 24} B per slice (normal equations in, slice out) + "
+                                f"{16 * r + 4} B per entry (h in, h out, level map); flop: complex Cholesky "
+                                f"4/3 D^3, 8 D^2 per triangular solve pair and per residual, 8 r^2 per entry"})
+    ms = avg_ms("eval")
+    if ms:
+        nt = int(prob.it.size)
+        fl = nt * 8 * (L * D + 2 * r)
+        af = fl / (ms * 1e-3) / 1e12
+        out.append({"kernel": "k_eval", "bound": "alu", "launch_ms": ms, "flop": fl,
+                    "achieved": af, "peak": fp32_meas, "unit": "TFLOP/s", "frac": af / fp32_meas,
+                    "per_unit": f"{8 * (L * D + 2 * r)} flop per test entry (L r x r complex products)",
+                    "note": "thread per test entry; the slices come from L2 (factors fit in it)"})
+    return out
+
+
 def lowrank_start(prob, bfc_mod, prec, gram=0):
     import synth
     A0, B0 = synth.random_lowrank_start(prob, prob.r)
@@ -539,6 +604,9 @@ def run_bfc(args, rank, world, local_rank):
                     "peak_source": ("measured FP64" if fp64_path else "measured FP32") +
                                    " FMA-chain peak (bfc_measure_alu_peaks, of measured)"}
 
+    kernel_roof = kernel_rooflines(prob, prof, stats, peaks, fp32_meas, roofline) \
+        if prec == bfc.PREC_C64 else None
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64+f64" if prec == bfc.PREC_C64 else "f64",
@@ -551,6 +619,7 @@ def run_bfc(args, rank, world, local_rank):
             "gpu_launches": launches,
             "kernels_ms": {k: round(v[1] / max(args.steps, 1), 4) for k, v in prof.items()},
             "roofline": roofline,
+            "kernel_rooflines": kernel_roof,
             "alu_peaks_measured": {"fp32_tflops": fp32_meas, "fp64_tflops": fp64_meas,
                                    "how": "bfc_measure_alu_peaks: dependent FMA chains on all SMs, best of 5"},
             "clocks": clocks,
