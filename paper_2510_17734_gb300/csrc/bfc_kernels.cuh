@@ -1231,17 +1231,53 @@ k_eval(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj, int64_t M
        const typename cvec<T>::type* __restrict__ zL, int L, int b, int64_t S,
        double2* __restrict__ out, const double2* __restrict__ tref, double* __restrict__ part)
 {
+    // A group of GS >= R lanes evaluates one entry: lane c keeps h_c and
+    // forms column c of h^T Z^{m}(k), so the group reads each slice row as
+    // one contiguous segment; h is passed around the group by shuffles.  The
+    // sums run over a in the same order as in eval_one.
     typedef typename cvec<T>::type V;
+    constexpr int GS = R <= 2 ? 2 : R <= 4 ? 4 : R <= 8 ? 8 : R <= 16 ? 16 : 32;
+    static_assert(R <= 32, "rank above 32");
+    constexpr int GPW = 32 / GS;
+    const int lane = threadIdx.x & 31, c = lane % GS, g = lane / GS;
+    const bool col = c < R;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double num = 0.0, den = 0.0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < M;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const V x = eval_one<T, R>(ii[e], jj[e], z1, Z, zL, L, b, S);
-        if (out) out[e] = to_d2(x);
-        if (tref) {
-            const double2 t = tref[e];
-            const double dx = t.x - (double)x.x, dy = t.y - (double)x.y;
-            num += dx * dx + dy * dy;
-            den += t.x * t.x + t.y * t.y;
+    for (int64_t base = warp0 * GPW; base < M; base += nwarps * GPW) {   // warp-uniform
+        const int64_t e = base + g;
+        const bool valid = e < M;
+        const int i = valid ? ii[e] : 0, j = valid ? jj[e] : 0;   // entry 0's indices stand in for the tail
+        V h = col ? z1[(size_t)i * R + c] : czero<V>();
+        const int pi = i / b, pj = j / b;
+        for (int m = 1; m <= L; ++m) {
+            const V* Zk = Z + ((size_t)(m - 1) * S + slice_of(pi, pj, m, L)) * R * R;
+            V acc = czero<V>();
+#pragma unroll
+            for (int a = 0; a < R; ++a) {
+                V ha;
+                ha.x = __shfl_sync(0xffffffffu, h.x, a, GS);
+                ha.y = __shfl_sync(0xffffffffu, h.y, a, GS);
+                if (col) cmac(acc, ha, Zk[a * R + c]);
+            }
+            h = acc;
+        }
+        V x = czero<V>();
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            V ha;
+            ha.x = __shfl_sync(0xffffffffu, h.x, a, GS);
+            ha.y = __shfl_sync(0xffffffffu, h.y, a, GS);
+            cmac(x, ha, zL[(size_t)j * R + a]);
+        }
+        if (valid && c == 0) {
+            if (out) out[e] = to_d2(x);
+            if (tref) {
+                const double2 t = tref[e];
+                const double dx = t.x - (double)x.x, dy = t.y - (double)x.y;
+                num += dx * dx + dy * dy;
+                den += t.x * t.x + t.y * t.y;
+            }
         }
     }
     if (part) {
