@@ -169,6 +169,32 @@ def test_gram_kernels_agree_over_sweeps(cfg3s):
         assert abs(a - b) <= 1e-3 * b
 
 
+@pytest.mark.parametrize("gram", [bfc.GRAM_TENSOR, bfc.GRAM_CUDA])
+@pytest.mark.parametrize("scale", [1e-6, 1e6])
+def test_rank8_gram_far_from_unit_scale(cfg3s, scale, gram):
+    """Data far from unit size keeps the complex64 parity of both Gram
+    kernels.  The problem is the unit-size one scaled exactly: values and
+    starting outer factors times `scale`, lambda times scale^2 (the
+    environments, the features and the right-hand sides scale with the data,
+    the middle slices do not)."""
+    p, X0 = cfg3s
+    X1 = X0.copy()
+    X1[:p.n * p.r] *= scale   # z1 leads the packed factors
+    t, tt, lam = p.t * scale, p.tt * scale, p.lam * scale * scale
+    Xo, st_o = oracle.als_sweep(p.n, p.L, p.b, p.r, lam, X1, p.i, p.j, t)
+    with bfc.Completion(p.n, p.L, p.b, p.r, lam, p.i, p.j, t, p.it, p.jt, tt,
+                        prec=bfc.PREC_C64, gram_impl=gram) as c:
+        c.set_factors(X1)
+        st = c.sweep()
+        Xg = c.get_factors()
+    tol = TOL[bfc.PREC_C64]
+    assert abs(st["objective"] - st_o["objective"]) <= tol * abs(st_o["objective"])
+    assert abs(st["train_rel_err"] - st_o["train_rel_err"]) <= tol * st_o["train_rel_err"]
+    xg = oracle.eval_entries(p.n, p.L, p.b, p.r, Xg, p.it, p.jt)
+    xo = oracle.eval_entries(p.n, p.L, p.b, p.r, Xo, p.it, p.jt)
+    assert rel_dev(xg, xo) <= 10 * tol
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_ten_sweeps_cfg1_final_test_error(cfg1, prec):
     p, X0 = cfg1
