@@ -276,7 +276,7 @@ k_outer_gram(const typename cvec<T>::type* __restrict__ A, const typename cvec<T
     constexpr int NI = NP + R;
     constexpr int IPL = (NI + 31) / 32;
     constexpr int WPB = 4;
-    __shared__ V a_s[WPB][32 * R];
+    __shared__ __align__(16) V a_s[WPB][32 * R];
     __shared__ V t_s[WPB][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int f = blockIdx.x * WPB + wib;
@@ -306,10 +306,20 @@ k_outer_gram(const typename cvec<T>::type* __restrict__ A, const typename cvec<T
     for (int base = s0; base < s1; base += 32) {
         const int cnt = min(32, s1 - base);
         __syncwarp();
-        if (lane < cnt) {
-#pragma unroll
-            for (int c = 0; c < R; ++c) a_s[wib][lane * R + c] = A[(size_t)(base + lane) * R + c];
-            t_s[wib][lane] = tv[base + lane];
+        // the chunk's rows are contiguous: copy them as one coalesced block
+        // (16-byte moves in complex64 at even rank, where every row starts on
+        // a 16-byte boundary)
+        {
+            const V* src = A + (size_t)base * R;
+            V* dst = a_s[wib];
+            const int nv = cnt * R;
+            if constexpr (sizeof(V) == 8 && R % 2 == 0) {
+                for (int x = lane; x < nv / 2; x += 32)
+                    reinterpret_cast<float4*>(dst)[x] = reinterpret_cast<const float4*>(src)[x];
+            } else {
+                for (int x = lane; x < nv; x += 32) dst[x] = src[x];
+            }
+            if (lane < cnt) t_s[wib][lane] = tv[base + lane];
         }
         __syncwarp();
         for (int e = 0; e < cnt; ++e) {
@@ -394,14 +404,23 @@ k_outer_post(const typename cvec<T>::type* __restrict__ A, const typename cvec<T
     const int f = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (f >= nfib) return;
     const int s0 = seg[f], s1 = seg[f + 1];
+    // complex64 rows of an even rank are written as 16-byte vectors
+    constexpr bool VEC = sizeof(V) == 8 && R % 2 == 0;
     V zf[R];
 #pragma unroll
     for (int c = 0; c < R; ++c) zf[c] = zt[(size_t)f * R + c];
     if (!COLS) {
         for (int p = s0 + lane; p < s1; p += 32) {
             const size_t o = (size_t)nxt[p] * R;
+            if constexpr (VEC) {
+                float4* d4 = reinterpret_cast<float4*>(Hn + o);
 #pragma unroll
-            for (int c = 0; c < R; ++c) Hn[o + c] = zf[c];
+                for (int c = 0; c < R / 2; ++c)
+                    d4[c] = make_float4(zf[2 * c].x, zf[2 * c].y, zf[2 * c + 1].x, zf[2 * c + 1].y);
+            } else {
+#pragma unroll
+                for (int c = 0; c < R; ++c) Hn[o + c] = zf[c];
+            }
         }
     } else {
         double num = 0.0, den = 0.0;
@@ -943,15 +962,25 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
     for (int k = blockIdx.x * C::WPB + wib; k < S; k += gridDim.x * C::WPB) {
         const V* K = rec + (size_t)k * (NPK + D);
         __syncwarp();
+        if constexpr (C::MIXED) {
+            // 16-byte moves: the record stride D (D + 3) / 2 is even for D = r^2,
+            // so every record starts on a 16-byte boundary
+            const float4* src = reinterpret_cast<const float4*>(K);
+            float4* dst = reinterpret_cast<float4*>(Lm);
+#pragma unroll 4
+            for (int q = lane; q < NPK / 2; q += 32) dst[q] = src[q];
+            if ((NPK & 1) && lane == 0) Lm[NPK - 1] = K[NPK - 1];
+        } else {
+            for (int q = lane; q < NPK; q += 32) Lm[q] = K[q];
+        }
+        __syncwarp();
         double tr = 0.0;
-        for (int p = lane; p < D; p += 32) tr += (double)K[tri(p, p)].x;
+        for (int p = lane; p < D; p += 32) tr += (double)Lm[tri(p, p)].x;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
         // lambda, raised to the ridge floor (relative to the mean diagonal) when set
         const double lambda = fmax(lambda_in, ridge * tr / D);
         const double tol = lambda > 0.0 ? 0.0 : 1e-14 * (tr + D * lambda);
-        for (int q = lane; q < NPK; q += 32) Lm[q] = K[q];
-        __syncwarp();
         if constexpr (C::MIXED) {
             // equilibrate: factor S (K + lambda I) S with S = diag(K_pp + lambda)^(-1/2)
             for (int p = lane; p < D; p += 32) {
