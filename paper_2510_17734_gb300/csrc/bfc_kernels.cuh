@@ -1057,17 +1057,33 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
                             df_sub_cmul(acc[s], make_float2(lamf, 0.f), sh[s], sl[s]);
                         }
                     }
-#pragma unroll 2
-                    for (int q = 0; q < D; ++q) {
-                        const float4 sq = s_df[q];
+                    // K_pq for 8 columns are fetched (from L2) before their products
+                    constexpr int QB = 8;
+                    for (int q0 = 0; q0 < D; q0 += QB) {
+                        V kv[NS][QB];
 #pragma unroll
-                        for (int s = 0; s < NS; ++s) {
-                            const int p = lane + 32 * s;
-                            if (p < D) {
-                                const bool lo = q <= p;
-                                const V kv = K[lo ? tri(p, q) : tri(q, p)];
-                                df_sub_cmul(acc[s], make_float2(kv.x, lo ? kv.y : -kv.y), make_float2(sq.x, sq.y),
-                                            make_float2(sq.z, sq.w));
+                        for (int i = 0; i < QB; ++i) {
+                            const int q = q0 + i;
+#pragma unroll
+                            for (int s = 0; s < NS; ++s) {
+                                const int p = lane + 32 * s;
+                                kv[s][i] = czero<V>();
+                                if (p < D && q < D) {
+                                    const bool lo = q <= p;
+                                    kv[s][i] = K[lo ? tri(p, q) : tri(q, p)];
+                                    if (!lo) kv[s][i].y = -kv[s][i].y;
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int i = 0; i < QB; ++i) {
+                            const int q = q0 + i;
+                            if (q < D) {
+                                const float4 sq = s_df[q];
+#pragma unroll
+                                for (int s = 0; s < NS; ++s)
+                                    if (lane + 32 * s < D)
+                                        df_sub_cmul(acc[s], kv[s][i], make_float2(sq.x, sq.y), make_float2(sq.z, sq.w));
                             }
                         }
                     }
