@@ -320,7 +320,7 @@ def batch_vs_fp64(bfc_mod, count=16, max_sweeps=30, tol_train=1e-4, tol_c64=3e-4
                               "plain_fp64": float(np.median([st["sweep"] for st in last64]))}}
 
 
-def run_learned(bfc_mod, n_train=64, n_test=8, epochs=200, max_sweeps=30, tol=1e-3, c_obs=36, with_nn=False):
+def run_learned(bfc_mod, n_train=64, n_test=8, epochs=2500, max_sweeps=30, tol=1e-3, c_obs=36, with_nn=False):
     """The learned-start workload: family n = 4096, L = 8, b = 16, r = 6,
     omega / (pi n) ~ U[1/16, 1/4], h ~ U[0.5, 2], |Omega| = c_obs n log2 n
     at the same sample positions for every member, lambda = 1e-7 (c_obs = 36
@@ -644,7 +644,7 @@ def run_bfc(args, rank, world, local_rank):
     if not args.no_batch and not args.n:
         line["batched"] = run_batched(bfc)
     if not args.no_learned and not args.n:
-        line["learned_start"] = run_learned(bfc)
+        line["learned_start"] = run_learned(bfc, n_train=args.learned_train, epochs=args.learned_epochs)
 
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -672,6 +672,8 @@ def main():
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance runs")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload run")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-start run")
+    ap.add_argument("--learned-train", type=int, default=64, help="training completions of the learned start")
+    ap.add_argument("--learned-epochs", type=int, default=2500, help="training epochs of the learned start")
     ap.add_argument("--gram", default="tensor", choices=["tensor", "cuda"],
                     help="precision-form middle-level Gram: tcgen05 tensor cores or CUDA cores")
     ap.add_argument("--n", type=int, default=0,
