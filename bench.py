@@ -178,6 +178,21 @@ def kernel_rooflines(prob, prof, stats, peaks, fp32_meas, main_roof):
                     "per_unit": f"{(npk + D) * 8 + D * 24} B per slice (normal equations in, slice out) + "
                                 f"{16 * r + 4} B per entry (h in, h out, level map); flop: complex Cholesky "
                                 f"4/3 D^3, 8 D^2 per triangular solve pair and per residual, 8 r^2 per entry"})
+    npo = r * (r + 1) // 2
+    outer = [("outer_rows_gram", "k_outer_gram (rows)", nnz * (8 * r + 8) + n * (npo + r) * 16,
+              f"{8 * r + 8} B per entry (w_0 row, value) + {(npo + r) * 16} B per row fiber (FP64 record)"),
+             ("outer_cols_gram", "k_outer_gram (columns)", nnz * (8 * r + 8) + n * (npo + r) * 16,
+              f"{8 * r + 8} B per entry (h_(L+1) row, value) + {(npo + r) * 16} B per column fiber"),
+             ("outer_rows_post", "k_outer_post (rows)", nnz * (8 * r + 4) + n * r * 8,
+              f"{8 * r + 4} B per entry (h_1 row written, level map) + {r * 8} B per fiber"),
+             ("outer_cols_post", "k_outer_post (columns)", nnz * (8 * r + 8) + n * r * 8,
+              f"{8 * r + 8} B per entry (h_(L+1) row, value) + {r * 8} B per fiber")]
+    for key, name, by, unit in outer:
+        ms = avg_ms(key)
+        if ms:
+            a = by / (ms * 1e-3) / 1e9
+            out.append({"kernel": name, "bound": "hbm", "launch_ms": ms, "bytes": by, "achieved": a,
+                        "peak": hbm, "unit": "GB/s", "frac": a / hbm, "per_unit": unit})
     ms = avg_ms("eval")
     if ms:
         nt = int(prob.it.size)
