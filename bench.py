@@ -574,6 +574,29 @@ def run_bfc(args, rank, world, local_rank):
         e2e_ms = float(t.item())
     e2e_value = world * prob.nnz / (e2e_ms * 1e-3)
 
+    # gradient sweep (Eqs. (grad_butterfly_1), (grad_butterfly_l),
+    # (grad_butterfly_last)): the full gradient of the regularized objective
+    # on the device (bfc_grad with no host copy), kernels timed by the
+    # library's CUDA events, the call by the host clock
+    for _ in range(2):
+        bfc.bfc_grad(c.ctx, True)
+    ng = 5
+    c.profile(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ng):
+        bfc.bfc_grad(c.ctx, True)
+    torch.cuda.synchronize()
+    grad_wall_ms = 1e3 * (time.perf_counter() - t0) / ng
+    gprof = c.profile_read()
+    c.profile(False)
+    grad_ms = sum(v[1] for v in gprof.values()) / ng
+    gradient = {"kernel_ms": grad_ms, "call_ms": grad_wall_ms,
+                "entries_per_s": world * prob.nnz / (grad_ms * 1e-3),
+                "kernels_ms": {k: round(v[1] / ng, 4) for k, v in gprof.items()},
+                "note": "one full gradient (all factors) per call, device-resident; call_ms includes the "
+                        "host synchronisation for the objective"}
+
     # roofline of the dominant kernel (per-slice normal equations + solve)
     launches = sum(int(st["launches"]) for st in stats)   # kernels launched by the timed sweeps
     mid_n, mid_ms = prof.get("mid_gram", (0, 0.0))
@@ -635,6 +658,7 @@ def run_bfc(args, rank, world, local_rank):
             "kernels_ms": {k: round(v[1] / max(args.steps, 1), 4) for k, v in prof.items()},
             "roofline": roofline,
             "kernel_rooflines": kernel_roof,
+            "gradient": gradient,
             "alu_peaks_measured": {"fp32_tflops": fp32_meas, "fp64_tflops": fp64_meas,
                                    "how": "bfc_measure_alu_peaks: dependent FMA chains on all SMs, best of 5"},
             "clocks": clocks,

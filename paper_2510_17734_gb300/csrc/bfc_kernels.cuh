@@ -1411,8 +1411,15 @@ k_grad_rows(const typename cvec<T>::type* __restrict__ W0, const typename cvec<T
 }
 
 // Middle level m: G^{m+1}(k) = sum r conj(h_m (x) w_m); h_{m+1} = h_m^T Z(k); r carried.
+// One CTA per slice at a time (persistent over slices), chunks of CH entries
+// staged in shared memory as contiguous blocks.  For D = R^2 <= 64 the 128
+// threads split the gradient components (q = t mod 64) and the chunk's
+// entries (two interleaved halves, t / 64); the halves are added at the end
+// of the slice.  The carried h rows are read back from global memory (the
+// chunk just loaded them, so they come from L1) and written as 16-byte
+// vectors in complex64 at even rank.
 template <typename T, int R>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4)
 k_grad_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>::type* __restrict__ Wm,
            const typename cvec<T>::type* __restrict__ Rc, const int32_t* __restrict__ seg,
            const int32_t* __restrict__ nxt, const typename cvec<T>::type* __restrict__ Zt,
@@ -1422,32 +1429,50 @@ k_grad_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
     typedef typename cvec<T>::type V;
     constexpr int D = R * R;
     constexpr int CH = 64;
+    constexpr int NG = D <= 64 ? 2 : 1;              // entry groups
+    constexpr int NQ = NG == 2 ? 1 : (D + 127) / 128;  // components per thread
+    constexpr bool VEC = sizeof(V) == 8 && R % 2 == 0;
     __shared__ V z_s[D];
-    __shared__ V h_s[CH * R], w_s[CH * R], r_s[CH];
+    __shared__ __align__(16) V h_s[CH * R];
+    __shared__ __align__(16) V w_s[CH * R];
+    __shared__ V r_s[CH];
+    __shared__ double2 g_s[NG == 2 ? 64 : 1];
+    const int tid = threadIdx.x;
+    const int grp = NG == 2 ? tid >> 6 : 0;
+    const int q0 = NG == 2 ? (tid & 63) : tid;
     for (int k = blockIdx.x; k < S; k += gridDim.x) {
         const int s0 = seg[k], s1 = seg[k + 1];
         __syncthreads();
-        for (int q = threadIdx.x; q < D; q += blockDim.x) z_s[q] = Zt[(size_t)k * D + q];
-        double2 g[(D + 127) / 128];
+        for (int q = tid; q < D; q += blockDim.x) z_s[q] = Zt[(size_t)k * D + q];
+        double2 g[NQ];
 #pragma unroll
-        for (int u = 0; u < (D + 127) / 128; ++u) g[u] = make_double2(0.0, 0.0);
+        for (int u = 0; u < NQ; ++u) g[u] = make_double2(0.0, 0.0);
         for (int base = s0; base < s1; base += CH) {
             const int cnt = min(CH, s1 - base);
             __syncthreads();
-            for (int q = threadIdx.x; q < cnt * R; q += blockDim.x) {
-                h_s[q] = H[(size_t)base * R + q];
-                w_s[q] = Wm[(size_t)base * R + q];
+            if constexpr (VEC) {
+                const float4* hs = reinterpret_cast<const float4*>(H + (size_t)base * R);
+                const float4* ws = reinterpret_cast<const float4*>(Wm + (size_t)base * R);
+                for (int x = tid; x < cnt * R / 2; x += blockDim.x) {
+                    reinterpret_cast<float4*>(h_s)[x] = hs[x];
+                    reinterpret_cast<float4*>(w_s)[x] = ws[x];
+                }
+            } else {
+                for (int x = tid; x < cnt * R; x += blockDim.x) {
+                    h_s[x] = H[(size_t)base * R + x];
+                    w_s[x] = Wm[(size_t)base * R + x];
+                }
             }
-            for (int q = threadIdx.x; q < cnt; q += blockDim.x) r_s[q] = Rc[base + q];
+            for (int x = tid; x < cnt; x += blockDim.x) r_s[x] = Rc[base + x];
             __syncthreads();
             // gradient components owned by threads
 #pragma unroll
-            for (int u = 0; u < (D + 127) / 128; ++u) {
-                const int q = threadIdx.x + 128 * u;
+            for (int u = 0; u < NQ; ++u) {
+                const int q = q0 + 128 * u;
                 if (q < D) {
                     const int pa = q / R, pc = q - pa * R;
                     V acc = czero<V>();
-                    for (int e = 0; e < cnt; ++e) {
+                    for (int e = grp; e < cnt; e += NG) {
                         const V a = cmul(h_s[e * R + pa], w_s[e * R + pc]);
                         cmacc(acc, a, r_s[e]);   // conj(a) r
                     }
@@ -1456,22 +1481,57 @@ k_grad_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
                 }
             }
             // carry h and r into the next order
-            for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            for (int e = tid; e < cnt; e += blockDim.x) {
                 const size_t o = (size_t)nxt[base + e];
+                const size_t src = (size_t)(base + e) * R;
+                V hv[R];
+                if constexpr (VEC) {
 #pragma unroll
-                for (int c = 0; c < R; ++c) {
-                    V acc2 = czero<V>();
+                    for (int c = 0; c < R / 2; ++c) {
+                        const float4 v4 = reinterpret_cast<const float4*>(H + src)[c];
+                        hv[2 * c].x = v4.x; hv[2 * c].y = v4.y;
+                        hv[2 * c + 1].x = v4.z; hv[2 * c + 1].y = v4.w;
+                    }
+                } else {
 #pragma unroll
-                    for (int a = 0; a < R; ++a) cmac(acc2, h_s[e * R + a], z_s[a * R + c]);
-                    Hn[o * R + c] = acc2;
+                    for (int c = 0; c < R; ++c) hv[c] = H[src + c];
+                }
+                // one pair of output columns at a time, stored at once (not
+                // unrolled, so the slice's R x R values are not all held in
+                // registers across entries)
+#pragma unroll 1
+                for (int c = 0; c < R; c += 2) {
+                    V a0 = czero<V>(), a1 = czero<V>();
+#pragma unroll
+                    for (int a = 0; a < R; ++a) {
+                        cmac(a0, hv[a], z_s[a * R + c]);
+                        if (c + 1 < R) cmac(a1, hv[a], z_s[a * R + c + 1]);
+                    }
+                    if constexpr (VEC) {
+                        reinterpret_cast<float4*>(Hn + o * R)[c / 2] = make_float4(a0.x, a0.y, a1.x, a1.y);
+                    } else {
+                        Hn[o * R + c] = a0;
+                        if (c + 1 < R) Hn[o * R + c + 1] = a1;
+                    }
                 }
                 Rn[o] = r_s[e];
             }
         }
+        if constexpr (NG == 2) {
+            // add the second entry group's sums to the first
+            __syncthreads();
+            if (grp == 1 && q0 < D) g_s[q0] = g[0];
+            __syncthreads();
+            if (grp == 0 && q0 < D) {
+                const double2 o2 = g_s[q0];
+                Gm[(size_t)k * D + q0] = make_double2(g[0].x + o2.x, g[0].y + o2.y);
+            }
+        } else {
 #pragma unroll
-        for (int u = 0; u < (D + 127) / 128; ++u) {
-            const int q = threadIdx.x + 128 * u;
-            if (q < D) Gm[(size_t)k * D + q] = g[u];
+            for (int u = 0; u < NQ; ++u) {
+                const int q = q0 + 128 * u;
+                if (q < D) Gm[(size_t)k * D + q] = g[u];
+            }
         }
     }
 }
