@@ -1349,6 +1349,48 @@ k_eval(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj, int64_t M
 // with z = x - t): the residual r_e is formed at the row level from the full
 // right environment (x = z1(i)^T w_0) and carried with h along the orders.
 
+// Sums of the row and column gradients: lane partials and the warp reduction
+// in the compute type (a lane sums about two entries of a fiber, so float
+// partials keep complex64 accuracy), FP64 in the FP64 path.
+template <typename T> struct GradAcc {
+    T x, y;
+    __device__ __forceinline__ void zero() { x = T(0); y = T(0); }
+    // += r conj(w)
+    template <typename V> __device__ __forceinline__ void add_r_conj(V r, V w)
+    {
+        x += r.x * w.x + r.y * w.y;
+        y += r.y * w.x - r.x * w.y;
+    }
+    __device__ __forceinline__ void warp_sum()
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+    }
+    __device__ __forceinline__ double2 d2() const { return make_double2((double)x, (double)y); }
+};
+
+// Loads row p of an R-column complex array (16-byte moves in complex64 at
+// even rank).
+template <typename V, int R>
+__device__ __forceinline__ void load_row_v(const V* __restrict__ A, size_t p, V (&v)[R])
+{
+    if constexpr (sizeof(V) == 8 && R % 2 == 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(A + p * R);
+#pragma unroll
+        for (int c = 0; c < R / 2; ++c) {
+            const float4 x = s4[c];
+            v[2 * c].x = x.x; v[2 * c].y = x.y;
+            v[2 * c + 1].x = x.z; v[2 * c + 1].y = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < R; ++c) v[c] = A[p * R + c];
+    }
+}
+
 // Rows: r = z1(i)^T w_0 - t, G1(i) = sum r conj(w_0); writes h_1 = z1(i) and r
 // into order 1; per-fiber sum of |r|^2 into part[f].
 template <typename T, int R>
@@ -1359,6 +1401,7 @@ k_grad_rows(const typename cvec<T>::type* __restrict__ W0, const typename cvec<T
             typename cvec<T>::type* __restrict__ Rn, double2* __restrict__ G1, double* __restrict__ part)
 {
     typedef typename cvec<T>::type V;
+    constexpr bool VEC = sizeof(V) == 8 && R % 2 == 0;
     const int lane = threadIdx.x & 31;
     const int f = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (f >= nfib) return;
@@ -1366,14 +1409,13 @@ k_grad_rows(const typename cvec<T>::type* __restrict__ W0, const typename cvec<T
     V z[R];
 #pragma unroll
     for (int c = 0; c < R; ++c) z[c] = z1t[(size_t)f * R + c];
-    double2 g[R];
+    GradAcc<T> g[R];
 #pragma unroll
-    for (int c = 0; c < R; ++c) g[c] = make_double2(0.0, 0.0);
+    for (int c = 0; c < R; ++c) g[c].zero();
     double fit = 0.0;
     for (int p = s0 + lane; p < s1; p += 32) {
         V w[R];
-#pragma unroll
-        for (int c = 0; c < R; ++c) w[c] = W0[(size_t)p * R + c];
+        load_row_v<V, R>(W0, (size_t)p, w);
         V x = czero<V>();
 #pragma unroll
         for (int c = 0; c < R; ++c) cmac(x, z[c], w[c]);
@@ -1383,29 +1425,26 @@ k_grad_rows(const typename cvec<T>::type* __restrict__ W0, const typename cvec<T
         rr.y = x.y - t.y;
         fit += (double)rr.x * (double)rr.x + (double)rr.y * (double)rr.y;
 #pragma unroll
-        for (int c = 0; c < R; ++c) {
-            // g += r conj(w)
-            g[c].x += (double)rr.x * (double)w[c].x + (double)rr.y * (double)w[c].y;
-            g[c].y += (double)rr.y * (double)w[c].x - (double)rr.x * (double)w[c].y;
-        }
+        for (int c = 0; c < R; ++c) g[c].add_r_conj(rr, w[c]);
         const size_t o = (size_t)nxt[p];
+        if constexpr (VEC) {
 #pragma unroll
-        for (int c = 0; c < R; ++c) Hn[o * R + c] = z[c];
+            for (int c = 0; c < R / 2; ++c)
+                reinterpret_cast<float4*>(Hn + o * R)[c] = make_float4(z[2 * c].x, z[2 * c].y, z[2 * c + 1].x,
+                                                                       z[2 * c + 1].y);
+        } else {
+#pragma unroll
+            for (int c = 0; c < R; ++c) Hn[o * R + c] = z[c];
+        }
         Rn[o] = rr;
     }
 #pragma unroll
-    for (int c = 0; c < R; ++c) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            g[c].x += __shfl_xor_sync(0xffffffffu, g[c].x, o);
-            g[c].y += __shfl_xor_sync(0xffffffffu, g[c].y, o);
-        }
-    }
+    for (int c = 0; c < R; ++c) g[c].warp_sum();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fit += __shfl_xor_sync(0xffffffffu, fit, o);
     if (lane == 0) {
 #pragma unroll
-        for (int c = 0; c < R; ++c) G1[(size_t)f * R + c] = g[c];
+        for (int c = 0; c < R; ++c) G1[(size_t)f * R + c] = g[c].d2();
         part[f] = fit;
     }
 }
@@ -1547,29 +1586,21 @@ k_grad_cols(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>
     const int f = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (f >= nfib) return;
     const int s0 = seg[f], s1 = seg[f + 1];
-    double2 g[R];
+    GradAcc<T> g[R];
 #pragma unroll
-    for (int c = 0; c < R; ++c) g[c] = make_double2(0.0, 0.0);
+    for (int c = 0; c < R; ++c) g[c].zero();
     for (int p = s0 + lane; p < s1; p += 32) {
         const V rr = Rc[p];
+        V h[R];
+        load_row_v<V, R>(H, (size_t)p, h);
 #pragma unroll
-        for (int c = 0; c < R; ++c) {
-            const V h = H[(size_t)p * R + c];
-            g[c].x += (double)rr.x * (double)h.x + (double)rr.y * (double)h.y;
-            g[c].y += (double)rr.y * (double)h.x - (double)rr.x * (double)h.y;
-        }
+        for (int c = 0; c < R; ++c) g[c].add_r_conj(rr, h[c]);
     }
 #pragma unroll
-    for (int c = 0; c < R; ++c) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            g[c].x += __shfl_xor_sync(0xffffffffu, g[c].x, o);
-            g[c].y += __shfl_xor_sync(0xffffffffu, g[c].y, o);
-        }
-    }
+    for (int c = 0; c < R; ++c) g[c].warp_sum();
     if (lane == 0) {
 #pragma unroll
-        for (int c = 0; c < R; ++c) GL[(size_t)f * R + c] = g[c];
+        for (int c = 0; c < R; ++c) GL[(size_t)f * R + c] = g[c].d2();
     }
 }
 
