@@ -423,16 +423,19 @@ k_outer_post(const typename cvec<T>::type* __restrict__ A, const typename cvec<T
             }
         }
     } else {
-        double num = 0.0, den = 0.0;
+        // lane sums in the compute type (about two entries per lane), the
+        // warp reduction in FP64
+        T numl = T(0), denl = T(0);
         for (int p = s0 + lane; p < s1; p += 32) {
             V x = czero<V>();
 #pragma unroll
             for (int c = 0; c < R; ++c) cmac(x, A[(size_t)p * R + c], zf[c]);
             const V t = tv[p];
-            const double dx = (double)t.x - (double)x.x, dy = (double)t.y - (double)x.y;
-            num += dx * dx + dy * dy;
-            den += (double)t.x * (double)t.x + (double)t.y * (double)t.y;
+            const T dx = t.x - x.x, dy = t.y - x.y;
+            numl += dx * dx + dy * dy;
+            denl += t.x * t.x + t.y * t.y;
         }
+        double num = (double)numl, den = (double)denl;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             num += __shfl_xor_sync(0xffffffffu, num, o);
@@ -1288,7 +1291,9 @@ k_eval(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj, int64_t M
     const bool col = c < R;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double num = 0.0, den = 0.0;
+    // a group leader sums about a dozen entries in the compute type; the
+    // reductions across lanes and warps run in FP64
+    T numl = T(0), denl = T(0);
     for (int64_t base = warp0 * GPW; base < M; base += nwarps * GPW) {   // warp-uniform
         const int64_t e = base + g;
         const bool valid = e < M;
@@ -1319,12 +1324,14 @@ k_eval(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj, int64_t M
             if (out) out[e] = to_d2(x);
             if (tref) {
                 const double2 t = tref[e];
-                const double dx = t.x - (double)x.x, dy = t.y - (double)x.y;
-                num += dx * dx + dy * dy;
-                den += t.x * t.x + t.y * t.y;
+                const T tx = (T)t.x, ty = (T)t.y;
+                const T dx = tx - x.x, dy = ty - x.y;
+                numl += dx * dx + dy * dy;
+                denl += tx * tx + ty * ty;
             }
         }
     }
+    double num = (double)numl, den = (double)denl;
     if (part) {
         __shared__ double sn[8], sd[8];
 #pragma unroll
