@@ -326,8 +326,10 @@ k_outer_gram(const typename cvec<T>::type* __restrict__ A, const typename cvec<T
             const V* ae = &a_s[wib][e * R];
 #pragma unroll
             for (int u = 0; u < IPL; ++u) {
-                if (iq[u] >= 0) cmacc(acc[u], ae[ip[u]], ae[iq[u]]);
-                else if (iq[u] == -2) cmacc(acc[u], ae[ip[u]], t_s[wib][e]);
+                if (ip[u] >= 0) {   // Gram item (iq >= 0) or right-hand side (iq == -2): one code path
+                    const V* bp = iq[u] >= 0 ? ae + iq[u] : &t_s[wib][e];
+                    cmacc(acc[u], ae[ip[u]], *bp);
+                }
             }
         }
         if (COMP) {
