@@ -591,7 +591,18 @@ def run_bfc(args, rank, world, local_rank):
     gprof = c.profile_read()
     c.profile(False)
     grad_ms = sum(v[1] for v in gprof.values()) / ng
-    gradient = {"kernel_ms": grad_ms, "call_ms": grad_wall_ms,
+    gm_n, gm_ms = gprof.get("grad_mid", (0, 0.0))
+    grad_mid_roof = None
+    if gm_n:
+        r_, S_ = prob.r, 1 << (prob.L + 1)
+        by = prob.nnz * (24 * r_ + 20) + S_ * r_ * r_ * 24
+        a = by / (gm_ms / gm_n * 1e-3) / 1e9
+        hbm_peak = load_peaks().get("hbm_gbs", 6800.0)
+        grad_mid_roof = {"kernel": "k_grad_mid", "bound": "hbm", "launch_ms": gm_ms / gm_n, "bytes": by,
+                         "achieved": a, "peak": hbm_peak, "unit": "GB/s", "frac": a / hbm_peak,
+                         "per_unit": f"{24 * r_ + 20} B per entry (h in and out, w, r in and out, level map) + "
+                                     f"{r_ * r_ * 24} B per slice (Z in, gradient out)"}
+    gradient = {"kernel_ms": grad_ms, "call_ms": grad_wall_ms, "roofline_grad_mid": grad_mid_roof,
                 "entries_per_s": world * prob.nnz / (grad_ms * 1e-3),
                 "kernels_ms": {k: round(v[1] / ng, 4) for k, v in gprof.items()},
                 "note": "one full gradient (all factors) per call, device-resident; call_ms includes the "
