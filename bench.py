@@ -532,7 +532,6 @@ def run_bfc(args, rank, world, local_rank):
         dist.barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    c.profile(True)
     stats = []
     with ClockSampler(local_rank) as clk:
         torch.cuda.synchronize()
@@ -544,9 +543,15 @@ def run_bfc(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     ms_total = ev0.elapsed_time(ev1)
+    ms_step = ms_total / args.steps
+    # per-kernel times: the same number of sweeps again with the library's
+    # per-kernel CUDA events on (kernels launched one by one, not from the
+    # captured sweep graph the timed sweeps replay)
+    c.profile(True)
+    for _ in range(args.steps):
+        c.sweep()
     prof = c.profile_read()
     c.profile(False)
-    ms_step = ms_total / args.steps
     if dist:
         t = torch.tensor([ms_step], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -168,7 +168,11 @@ bfc_status bfc_eval(bfc_ctx* ctx, int64_t m, const int32_t* i, const int32_t* j,
  * values of all other factors (complex normal equations
  * K = sum conj(a) a^T + lambda I, y = sum conj(a) t).  A system whose
  * Cholesky pivot falls to <= 0 (<= 1e-14 trace(K) when lambda = 0) keeps its
- * old values and is counted in singular_slices.  `out` may be NULL. */
+ * old values and is counted in singular_slices.  `out` may be NULL.
+ * Unless kernel profiling is on, the first call captures the sweep's kernels
+ * into a CUDA graph on the context stream and every call launches that graph
+ * (same kernels, same order); a stream that cannot be captured runs them
+ * directly. */
 bfc_status bfc_als_sweep(bfc_ctx* ctx, bfc_sweep_stats* out);
 
 /* Gradient of f with respect to all parameters (Eqs. (grad_butterfly_1),

@@ -418,11 +418,24 @@ static bfc_status sweep_finish(Ctx* c, bfc_sweep_stats* out, int64_t launched)
     return BFC_OK;
 }
 
-static bfc_status sweep_impl(Ctx* c, bfc_sweep_stats* out)
+static bfc_status capture_sweep(Ctx* c);
+
+// One sweep and its statistics.  With `replay`, a context that is not
+// profiling launches its captured sweep graph (captured on first use; the
+// kernels and their order are those of the direct path), which removes the
+// per-kernel launch cost of the 12 + 5 L kernels.
+static bfc_status sweep_impl(Ctx* c, bfc_sweep_stats* out, bool replay = false)
 {
     const int64_t launched0 = c->n_launch;
+    if (replay && !c->prof) BFC_TRY(capture_sweep(c));
+    const bool graph = replay && !c->prof && c->sweep_graph && c->graph_tc == c->gram_tc;
     BFC_CK(c, cudaEventRecord(c->ev0, c->stream));
-    BFC_TRY(sweep_enqueue(c));
+    if (graph) {
+        BFC_CK(c, cudaGraphLaunch(c->sweep_graph, c->stream));
+        c->n_launch += c->graph_launches;
+    } else {
+        BFC_TRY(sweep_enqueue(c));
+    }
     BFC_CK(c, cudaEventRecord(c->ev1, c->stream));
     return sweep_finish(c, out, c->n_launch - launched0);
 }
@@ -719,7 +732,7 @@ bfc_status bfc_als_sweep(bfc_ctx* ctx, bfc_sweep_stats* out)
 {
     Ctx* c = (Ctx*)ctx;
     if (!c) return BFC_EINVAL;
-    return sweep_impl(c, out);
+    return sweep_impl(c, out, true);
 }
 
 bfc_status bfc_grad(bfc_ctx* ctx, int32_t include_reg, double* grad_packed, double* objective)
@@ -912,7 +925,7 @@ bfc_status bfc_complete(bfc_ctx* ctx, bfc_sweep_stats* history, int32_t history_
     int done = 0;
     for (int s = 0; s < c->P.max_sweeps; ++s) {
         bfc_sweep_stats st{};
-        BFC_TRY(sweep_impl(c, &st));
+        BFC_TRY(sweep_impl(c, &st, true));
         if (history && done < history_cap) history[done] = st;
         ++done;
         if (st.train_rel_err < c->P.tol) break;
