@@ -782,7 +782,27 @@ __device__ bool warp_chol(E* Lm, int D, S tol, int lane)
             const int r = owned_row(s, lane);
             if (r >= j1 && r < D) {
                 E* rowp = Lm + tri(r, 0);
-                for (int q = j1; q <= r; ++q) {
+                // two columns per step: both elements and both panel rows are
+                // loaded before either element is stored (independent chains)
+                int q = j1;
+                for (; q + 1 <= r; q += 2) {
+                    const E* qa = Lm + tri(q, 0) + j0;
+                    const E* qb = Lm + tri(q + 1, 0) + j0;
+                    E ca = rowp[q], cb = rowp[q + 1];
+                    E va[NBK], vb[NBK];
+#pragma unroll
+                    for (int k = 0; k < NBK; ++k)
+                        if (k < nb) { va[k] = qa[k]; vb[k] = qb[k]; }
+#pragma unroll
+                    for (int k = 0; k < NBK; ++k)
+                        if (k < nb) {
+                            csub_mul_conj(ca, x[s][k], va[k]);
+                            csub_mul_conj(cb, x[s][k], vb[k]);
+                        }
+                    rowp[q] = ca;
+                    rowp[q + 1] = cb;
+                }
+                if (q <= r) {
                     const E* qrow = Lm + tri(q, 0) + j0;
                     E cur = rowp[q];
 #pragma unroll
