@@ -266,6 +266,28 @@ def test_complete_stops_at_tolerance(cfg1):
     assert all(h["train_rel_err"] >= 5e-3 for h in hist[:-1])
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_graph_replay_equals_direct_launches(cfg2s, prec):
+    """bfc_als_sweep replays a captured CUDA graph of the sweep unless kernel
+    profiling is on; both paths run the same kernels in the same order, so
+    three sweeps from the same start give bit-identical factors, errors and
+    launch counts."""
+    p, X0 = cfg2s
+    out = {}
+    for profiled in (True, False):
+        with make(p, prec) as c:
+            c.set_factors(X0)
+            c.profile(profiled)
+            hist = [c.sweep() for _ in range(3)]
+            out[profiled] = (c.get_factors(), hist)
+    (Xd, hd), (Xg, hg) = out[True], out[False]
+    assert np.array_equal(Xd.view(np.float64), Xg.view(np.float64))
+    for a, b_ in zip(hd, hg):
+        assert a["train_rel_err"] == b_["train_rel_err"]
+        assert a["test_rel_err"] == b_["test_rel_err"]
+        assert a["launches"] == b_["launches"]
+
+
 # ------------------------------------------------------------ edge cases
 
 @pytest.mark.parametrize("prec", PRECS)
