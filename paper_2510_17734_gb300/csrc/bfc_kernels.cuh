@@ -1496,7 +1496,7 @@ k_grad_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
 {
     typedef typename cvec<T>::type V;
     constexpr int D = R * R;
-    constexpr int CH = 64;
+    constexpr int CH = 128;
     constexpr int NG = D <= 64 ? 2 : 1;              // entry groups
     constexpr int NQ = NG == 2 ? 1 : (D + 127) / 128;  // components per thread
     constexpr bool VEC = sizeof(V) == 8 && R % 2 == 0;
