@@ -125,6 +125,23 @@ def als_flops_per_entry(r: int) -> int:
     return 8 * (r * r * (r * r + 1) // 2 + r * r)
 
 
+def max_over_ranks(x: float, dist_mod, device) -> float:
+    """The largest value of x over all ranks (a job's step time is its slowest
+    rank's); x itself when there is no process group."""
+    if dist_mod is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms_step: float) -> float:
+    """Whole-job units per second: every replica processes units_per_rank
+    units per step of ms_step (the max over ranks)."""
+    return world * units_per_rank / (ms_step * 1e-3)
+
+
 def kernel_rooflines(prob, prof, stats, peaks, fp32_meas, main_roof):
     """Per-kernel algorithmic work against the measured peaks (complex64
     precision form), from the library's CUDA-event timers of the timed sweeps.
@@ -552,11 +569,8 @@ def run_bfc(args, rank, world, local_rank):
         c.sweep()
     prof = c.profile_read()
     c.profile(False)
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * prob.nnz / (ms_step * 1e-3)
+    ms_step = max_over_ranks(ms_step, dist, dev)
+    value = job_throughput(prob.nnz, world, ms_step)
 
     # end to end through the public API with host buffers (pinned)
     P = c.P
@@ -573,11 +587,8 @@ def run_bfc(args, rank, world, local_rank):
         bfc.bfc_get_factors(c.ctx, host_out)
     torch.cuda.synchronize()
     e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * prob.nnz / (e2e_ms * 1e-3)
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+    e2e_value = job_throughput(prob.nnz, world, e2e_ms)
 
     # gradient sweep (Eqs. (grad_butterfly_1), (grad_butterfly_l),
     # (grad_butterfly_last)): the full gradient of the regularized objective
