@@ -114,9 +114,9 @@ k_env_right(const typename cvec<T>::type* __restrict__ Win,
         __syncthreads();
         for (int q = threadIdx.x; q < R * R; q += blockDim.x) z[q] = Zm[(size_t)k * R * R + q];
         __syncthreads();
-        for (int p = s0 + threadIdx.x; p < s1; p += blockDim.x) {
-            V w[R];
-            if constexpr (VEC) {
+        if constexpr (VEC) {
+            for (int p = s0 + threadIdx.x; p < s1; p += blockDim.x) {
+                V w[R];
                 const float4* src = reinterpret_cast<const float4*>(Win + (size_t)p * R);
 #pragma unroll
                 for (int c = 0; c < R / 2; ++c) {
@@ -124,27 +124,36 @@ k_env_right(const typename cvec<T>::type* __restrict__ Win,
                     w[2 * c].x = v.x; w[2 * c].y = v.y;
                     w[2 * c + 1].x = v.z; w[2 * c + 1].y = v.w;
                 }
-            } else {
+                const size_t o = (size_t)prv[p] * R;
+                V res[R];
 #pragma unroll
-                for (int c = 0; c < R; ++c) w[c] = Win[(size_t)p * R + c];
-            }
-            const size_t o = (size_t)prv[p] * R;
-            V res[R];
+                for (int a = 0; a < R; ++a) {
+                    V acc = czero<V>();
 #pragma unroll
-            for (int a = 0; a < R; ++a) {
-                V acc = czero<V>();
-#pragma unroll
-                for (int c = 0; c < R; ++c) cmac(acc, z[a * R + c], w[c]);
-                res[a] = acc;
-            }
-            if constexpr (VEC) {
+                    for (int c = 0; c < R; ++c) cmac(acc, z[a * R + c], w[c]);
+                    res[a] = acc;
+                }
                 float4* dst = reinterpret_cast<float4*>(Wout + o);
 #pragma unroll
                 for (int a = 0; a < R / 2; ++a)
                     dst[a] = make_float4(res[2 * a].x, res[2 * a].y, res[2 * a + 1].x, res[2 * a + 1].y);
-            } else {
+            }
+        } else {
+            for (int p = s0 + threadIdx.x; p < s1; p += blockDim.x) {
+                V w[R];
 #pragma unroll
-                for (int a = 0; a < R; ++a) Wout[o + a] = res[a];
+                for (int c = 0; c < R; ++c) w[c] = Win[(size_t)p * R + c];
+                const size_t o = (size_t)prv[p] * R;
+                // one output value at a time, stored at once (not unrolled,
+                // so the slice is read from shared memory, not held in
+                // registers across entries)
+#pragma unroll 1
+                for (int a = 0; a < R; ++a) {
+                    V acc = czero<V>();
+#pragma unroll
+                    for (int c = 0; c < R; ++c) cmac(acc, z[a * R + c], w[c]);
+                    Wout[o + a] = acc;
+                }
             }
         }
     }
