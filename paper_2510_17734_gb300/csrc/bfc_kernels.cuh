@@ -950,9 +950,11 @@ template <typename T, int R> struct SolveCfg {
     // per warp: factor (compute type, padded to 16 bytes), FP64 solution
     // vector, new slice (compute type)
     static constexpr size_t LBYTES = ((size_t)NPK * sizeof(typename cvec<T>::type) + 15) / 16 * 16;
-    static constexpr size_t WBYTES = (LBYTES + (size_t)D * sizeof(double2) +
-                                      (size_t)D * sizeof(typename cvec<T>::type) + (size_t)D * sizeof(T) + 15) /
-                                     16 * 16;
+    static constexpr size_t WCORE = (LBYTES + (size_t)D * sizeof(double2) +
+                                     (size_t)D * sizeof(typename cvec<T>::type) + (size_t)D * sizeof(T) + 15) /
+                                    16 * 16;
+    // + one mbarrier per warp (the bulk copy of the record), padded to 16 bytes
+    static constexpr size_t WBYTES = WCORE + 16;
     static constexpr int WPB0 = (int)((96 * 1024) / WBYTES);
     static constexpr int WPB = WPB0 < 1 ? 1 : (WPB0 > 4 ? 4 : WPB0);
     static constexpr size_t SMEM = WBYTES * WPB;
@@ -979,9 +981,11 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
             typename cvec<T>::type* __restrict__ Hn, double2* __restrict__ Zd,
             typename cvec<T>::type* __restrict__ Zt, double2* __restrict__ fb, double lambda_in, double ridge,
             unsigned long long* __restrict__ nsing, unsigned long long* __restrict__ nfb,
-            unsigned long long* __restrict__ nsteps, int32_t* __restrict__ fblist, int S)
+            unsigned long long* __restrict__ nsteps, int32_t* __restrict__ fblist, int S,
+            unsigned long long* __restrict__ terr)
 {
-    // nfb: slices handed to the FP64 fallback (length of fblist); nsteps: refinement steps
+    // nfb: slices handed to the FP64 fallback (length of fblist); nsteps: refinement steps;
+    // terr: raised when the bulk copy of a record does not complete within the wait limit
     typedef typename cvec<T>::type V;
     typedef SolveCfg<T, R> C;
     constexpr int D = C::D, NPK = C::NPK, NS = C::NS;
@@ -992,13 +996,52 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
     double2* s_d = (double2*)(base + C::LBYTES);
     V* zt_s = (V*)(s_d + D);
     T* sc_s = (T*)(zt_s + D);  // Jacobi scaling of the complex64 factorization
+    // The record's K block reaches shared memory by one bulk copy (the copy
+    // engine, completion counted on a per-warp mbarrier) in the precision
+    // form; the wait is bounded.
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(base + C::WCORE);
+    constexpr uint32_t KBULK = (uint32_t)((NPK & ~1) * sizeof(V));   // a multiple of 16 bytes
+    constexpr bool BULK = C::MIXED && KBULK >= 16;
+    uint32_t phase = 0;
+    if constexpr (BULK) {
+        if (lane == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncwarp();
+    }
 
     for (int k = blockIdx.x * C::WPB + wib; k < S; k += gridDim.x * C::WPB) {
         const V* K = rec + (size_t)k * (NPK + D);
         __syncwarp();
-        if constexpr (C::MIXED) {
-            // 16-byte moves: the record stride D (D + 3) / 2 is even for D = r^2,
-            // so every record starts on a 16-byte boundary
+        if constexpr (BULK) {
+            // the record stride D (D + 3) / 2 is even for D = r^2, so every
+            // record starts on a 16-byte boundary; the previous slice's
+            // accesses to the factor area are ordered before the copy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
+                             ::"r"(bar), "r"(KBULK) : "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             ::"r"((uint32_t)__cvta_generic_to_shared(Lm)), "l"(K), "r"(KBULK), "r"(bar)
+                             : "memory");
+            }
+            if ((NPK & 1) && lane == 0) Lm[NPK - 1] = K[NPK - 1];
+            bool done = false;
+            for (uint32_t it = 0; it < (1u << 22) && !done; ++it) {
+                uint32_t ok;
+                asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n"
+                             "selp.u32 %0, 1, 0, p;\n}\n"
+                             : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
+                done = ok != 0;
+            }
+            phase ^= 1u;
+            if (!done) {
+                // the copy did not complete: report it; the slice's results are undefined
+                if (lane == 0) atomicExch(terr, 1ull);
+            }
+        } else if constexpr (C::MIXED) {
             const float4* src = reinterpret_cast<const float4*>(K);
             float4* dst = reinterpret_cast<float4*>(Lm);
 #pragma unroll 4
