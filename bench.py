@@ -14,11 +14,19 @@ working set (about 4.5 GB of environments, values and orders) is far larger
 than L2, so no flush is needed between steps.
 
 Lines printed (one JSON line, rank 0):
-  value      entries/s of the timed sweeps, whole job (sum over ranks)
+  value      entries/s of the timed sweeps (replays of the captured sweep
+             graph), whole job (sum over ranks)
   e2e        the same through the public API with host buffers: every step
              copies the factors from pinned host memory, sweeps, and copies
              the factors and statistics back
+  kernels_ms per-kernel CUDA-event times of the same number of sweeps run
+             again with the library's profiling on
   roofline   dominant kernel (the per-slice normal-equation kernel)
+  kernel_rooflines  every kernel above 1 % of a sweep against its bound
+  gradient   one full gradient (bfc_grad, device-resident) and the roofline
+             of its middle-level kernel
+  time_to_1e-3_test_error, batched, learned_start  the three forms against
+             plain FP64 ALS on the same GPU
   cpu_baseline  the complex128 oracle timed on a bounded sample (rank 0)
 Multi-GPU: every rank runs an independent replica (the single problem does
 not shard without an exchange step); value is the sum over ranks.
