@@ -1,6 +1,7 @@
-"""Host logic of bench.py's multi-GPU path (replicas, one process per GPU):
-the step time is the max over ranks and the job's throughput sums the
-replicas' work.  Run as two gloo processes on the CPU."""
+"""Host logic of bench.py.  The multi-GPU path (replicas, one process per
+GPU): the step time is the max over ranks and the job's throughput sums the
+replicas' work, run as two gloo processes on the CPU.  The per-kernel
+roofline rows: algorithmic work over the measured kernel time."""
 import os
 import socket
 
@@ -47,3 +48,27 @@ def test_max_over_ranks_and_job_throughput_two_gloo_ranks():
 def test_single_process_passes_through():
     assert bench.max_over_ranks(12.5, None, "cpu") == 12.5
     assert bench.job_throughput(3774874, 1, 25.0) == pytest.approx(3774874 / 25e-3)
+
+
+def test_kernel_rooflines_arithmetic():
+    """Per-kernel roofline rows: algorithmic bytes or flops per launch over
+    the mean CUDA-event time of that kernel, against the given peaks."""
+    import synth
+    p = synth.config(3)                     # n = 65536, L = 12, r = 8
+    nnz, S = p.nnz, 1 << (p.L + 1)
+    prof = {"env_right": (24, 24 * 0.1), "mid_gram": (24, 24 * 1.0), "mid_solve": (24, 24 * 0.5),
+            "eval": (2, 2 * 0.25)}
+    stats = [{"refine_steps": p.L * S}, {"refine_steps": p.L * S}]
+    main = {"kernel": "k_mid_gram_tc (tensor)", "bound": "tensor", "peak": 800.0, "frac": 0.06}
+    rows = {r["kernel"]: r for r in bench.kernel_rooflines(p, prof, stats, {"hbm_gbs": 6000.0}, 80.0, main)}
+    env = rows["k_env_right"]
+    assert env["bytes"] == nnz * (16 * 8 + 4) + S * 64 * 8
+    assert env["achieved"] == pytest.approx(env["bytes"] / 0.1e-3 / 1e9)
+    assert env["frac"] == pytest.approx(env["achieved"] / 6000.0)
+    gram = rows["k_mid_gram_tc"]
+    assert gram["flop"] == nnz * 8 * (64 * 65 // 2 + 64)
+    assert gram["fp32_frac"] == pytest.approx(gram["flop"] / 1e-3 / 1e12 / 80.0)
+    solve = rows["k_mid_solve"]
+    assert solve["refine_steps_per_slice"] == pytest.approx(1.0)
+    assert solve["bytes"] == S * (2080 + 64) * 8 + nnz * (16 * 8 + 4) + S * 64 * 24 + 4 * (S + 1)
+    assert "k_eval" in rows and rows["k_eval"]["launch_ms"] == pytest.approx(0.25)
