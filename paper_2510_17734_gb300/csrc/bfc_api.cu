@@ -356,11 +356,12 @@ static bfc_status collect_stats(Ctx* c, bfc_sweep_stats* out, float ms)
     BFC_CK(c, cudaMemcpyAsync(hc, c->d_count, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
     BFC_TRY(sync(c));
     if (hc[5] != 0) {
-        // a bounded wait inside the tensor-core Gram expired: the sweep's
-        // results are undefined; clear the flag so the context stays usable
+        // a bounded wait inside the tensor-core Gram or on a bulk copy of the
+        // solve expired: the sweep's results are undefined; clear the flag so
+        // the context stays usable
         BFC_CK(c, cudaMemsetAsync(c->d_count + 5, 0, sizeof(unsigned long long), c->stream));
         BFC_TRY(sync(c));
-        return fail(c, BFC_ETIMEOUT, "tensor-core Gram: a bounded device wait expired");
+        return fail(c, BFC_ETIMEOUT, "a bounded device wait expired (tensor-core Gram or bulk copy)");
     }
     if (out) {
         out->sweep = c->sweeps_done;
@@ -496,8 +497,18 @@ static bfc_status grad_into(Ctx* c, int include_reg, double2* G, double* hs)
     BFC_TRY(factor_sumsq(c, 2));
     if (include_reg) launch_axpy((double*)G, (const double*)c->z1d, c->P.lambda, 2 * c->Pn, c->stream);
     BFC_LAUNCH_CHECK(c, "grad tail");
+    unsigned long long terr = 0;
     BFC_CK(c, cudaMemcpyAsync(hs, c->d_scalars, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    return sync(c);
+    BFC_CK(c, cudaMemcpyAsync(&terr, c->d_count + 5, sizeof(terr), cudaMemcpyDeviceToHost, c->stream));
+    BFC_TRY(sync(c));
+    if (terr != 0) {
+        // a bounded wait on a bulk copy of the gradient sweep expired: the
+        // gradient is undefined; clear the flag so the context stays usable
+        BFC_CK(c, cudaMemsetAsync(c->d_count + 5, 0, sizeof(unsigned long long), c->stream));
+        BFC_TRY(sync(c));
+        return fail(c, BFC_ETIMEOUT, "gradient sweep: a bounded device wait expired");
+    }
+    return BFC_OK;
 }
 
 // Dot product of two device vectors of n doubles, returned on the host.

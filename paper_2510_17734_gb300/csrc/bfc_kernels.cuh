@@ -1532,7 +1532,8 @@ k_grad_rows(const typename cvec<T>::type* __restrict__ W0, const typename cvec<T
 
 // Middle level m: G^{m+1}(k) = sum r conj(h_m (x) w_m); h_{m+1} = h_m^T Z(k); r carried.
 // One CTA per slice at a time (persistent over slices), chunks of CH entries
-// staged in shared memory as contiguous blocks.  For D = R^2 <= 64 the 128
+// staged in shared memory as contiguous blocks (bulk copies in complex64 at
+// even rank).  For D = R^2 <= 64 the 128
 // threads split the gradient components (q = t mod 64) and the chunk's
 // entries (two interleaved halves, t / 64); the halves are added at the end
 // of the slice.  The carried h rows are read back from global memory (the
@@ -1544,7 +1545,7 @@ k_grad_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
            const typename cvec<T>::type* __restrict__ Rc, const int32_t* __restrict__ seg,
            const int32_t* __restrict__ nxt, const typename cvec<T>::type* __restrict__ Zt,
            typename cvec<T>::type* __restrict__ Hn, typename cvec<T>::type* __restrict__ Rn,
-           double2* __restrict__ Gm, int S)
+           double2* __restrict__ Gm, int S, unsigned long long* __restrict__ terr)
 {
     typedef typename cvec<T>::type V;
     constexpr int D = R * R;
@@ -1557,9 +1558,22 @@ k_grad_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
     __shared__ __align__(16) V w_s[CH * R];
     __shared__ V r_s[CH];
     __shared__ double2 g_s[NG == 2 ? 64 : 1];
+    // complex64 at even rank: a chunk's h and w rows (contiguous, 16-byte
+    // multiples) arrive by two bulk copies counted on one mbarrier (the wait
+    // is bounded; on expiry *terr is raised and the results are undefined)
+    __shared__ __align__(8) unsigned long long cbar;
     const int tid = threadIdx.x;
     const int grp = NG == 2 ? tid >> 6 : 0;
     const int q0 = NG == 2 ? (tid & 63) : tid;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&cbar);
+    uint32_t phase = 0;
+    if constexpr (VEC) {
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
     for (int k = blockIdx.x; k < S; k += gridDim.x) {
         const int s0 = seg[k], s1 = seg[k + 1];
         __syncthreads();
@@ -1569,21 +1583,41 @@ k_grad_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
         for (int u = 0; u < NQ; ++u) g[u] = make_double2(0.0, 0.0);
         for (int base = s0; base < s1; base += CH) {
             const int cnt = min(CH, s1 - base);
-            __syncthreads();
             if constexpr (VEC) {
-                const float4* hs = reinterpret_cast<const float4*>(H + (size_t)base * R);
-                const float4* ws = reinterpret_cast<const float4*>(Wm + (size_t)base * R);
-                for (int x = tid; x < cnt * R / 2; x += blockDim.x) {
-                    reinterpret_cast<float4*>(h_s)[x] = hs[x];
-                    reinterpret_cast<float4*>(w_s)[x] = ws[x];
+                // every thread's reads of the previous chunk are ordered
+                // before the copy engine overwrites the buffers
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                if (tid == 0) {
+                    const uint32_t bytes = (uint32_t)(cnt * R * sizeof(V));
+                    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
+                                 ::"r"(bar), "r"(2 * bytes) : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"((uint32_t)__cvta_generic_to_shared(h_s)), "l"(H + (size_t)base * R), "r"(bytes),
+                                 "r"(bar) : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"((uint32_t)__cvta_generic_to_shared(w_s)), "l"(Wm + (size_t)base * R), "r"(bytes),
+                                 "r"(bar) : "memory");
                 }
+                for (int x = tid; x < cnt; x += blockDim.x) r_s[x] = Rc[base + x];
+                bool done = false;
+                for (uint32_t it = 0; it < (1u << 22) && !done; ++it) {
+                    uint32_t ok;
+                    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n"
+                                 "selp.u32 %0, 1, 0, p;\n}\n"
+                                 : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
+                    done = ok != 0;
+                }
+                phase ^= 1u;
+                if (!done && tid == 0) atomicExch(terr, 1ull);
             } else {
+                __syncthreads();
                 for (int x = tid; x < cnt * R; x += blockDim.x) {
                     h_s[x] = H[(size_t)base * R + x];
                     w_s[x] = Wm[(size_t)base * R + x];
                 }
+                for (int x = tid; x < cnt; x += blockDim.x) r_s[x] = Rc[base + x];
             }
-            for (int x = tid; x < cnt; x += blockDim.x) r_s[x] = Rc[base + x];
             __syncthreads();
             // gradient components owned by threads
 #pragma unroll

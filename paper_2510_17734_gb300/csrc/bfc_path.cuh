@@ -186,7 +186,8 @@ template <typename T, int R> struct Path {
             ProfScope ps(c, "grad_mid");
             k_grad_mid<T, R><<<g, 128, 0, c->stream>>>(Hb[in], W + (size_t)m * NR, Rb[in], c->seg[m], c->nxt[m],
                                                         (const V*)c->Zt + (size_t)(m - 1) * S * R * R, Hb[out],
-                                                        Rb[out], GZ + (size_t)(m - 1) * S * R * R, (int)S);
+                                                        Rb[out], GZ + (size_t)(m - 1) * S * R * R, (int)S,
+                                                        c->d_count + 5);
         }
         BFC_LAUNCH_CHECK(c, "grad_mid");
         {
