@@ -964,16 +964,18 @@ template <typename T, int R> struct SolveCfg {
 };
 
 // Middle level m, stage 2 (solve + left update): one warp per slice.
-// Precision form (float): complex64 Cholesky of the Jacobi-equilibrated
-// S (K + lambda I) S, complex64 solve, then up to three steps of iterative
-// refinement: the residual y - (K + lambda I) s is formed in double-float
-// arithmetic (TwoSum-compensated float pairs, rows spread over the lanes)
-// against a solution kept as a double-float pair, and the correction goes
-// through the complex64 factor.  If the factorization breaks down or the
-// refinement does not contract, the slice goes on a list for the FP64
-// Cholesky of k_mid_fallback.  FP64 path (double): FP64 Cholesky directly.  The slice is written row-major in FP64
-// and the compute type; then h_{m+1}(e) = h_m(e)^T Z^{m+1}(k) for the slice's
-// entries is scattered into order m+1.  A singular system keeps its old slice.
+// Precision form (float): the slice's K block arrives in shared memory by one
+// bulk copy; complex64 Cholesky of the Jacobi-equilibrated S (K + lambda I) S,
+// complex64 solve, then up to three steps of iterative refinement: the
+// residual y - (K + lambda I) s is formed in double-float arithmetic
+// (TwoSum-compensated float pairs, rows spread over the lanes) against a
+// solution kept as a double-float pair, and the correction goes through the
+// complex64 factor.  If the factorization breaks down or the refinement does
+// not contract, the slice goes on a list for the FP64 Cholesky of
+// k_mid_fallback.  FP64 path (double): FP64 Cholesky directly.  The slice is
+// written row-major in FP64 and the compute type; then
+// h_{m+1}(e) = h_m(e)^T Z^{m+1}(k) for the slice's entries is scattered into
+// order m+1.  A singular system keeps its old slice.
 template <typename T, int R>
 __global__ void __launch_bounds__(32 * SolveCfg<T, R>::WPB, SolveCfg<T, R>::MINB)
 k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<T>::type* __restrict__ H,
