@@ -180,7 +180,9 @@ bfc_status bfc_als_sweep(bfc_ctx* ctx, bfc_sweep_stats* out);
  * df/dRe + i df/dIm; the regularization term lambda S is added when
  * include_reg is nonzero.  grad_packed (may be NULL) receives the packed
  * gradient, *objective (may be NULL) the value of f (with or without the
- * regularization term, matching include_reg). */
+ * regularization term, matching include_reg).  BFC_ETIMEOUT if a bounded
+ * device wait (the bulk copies of the middle levels) expired; the gradient
+ * is then undefined and the context stays usable. */
 bfc_status bfc_grad(bfc_ctx* ctx, int32_t include_reg, double* grad_packed,
                     double* objective);
 
