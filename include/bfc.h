@@ -172,7 +172,9 @@ bfc_status bfc_eval(bfc_ctx* ctx, int64_t m, const int32_t* i, const int32_t* j,
  * Unless kernel profiling is on, the first call captures the sweep's kernels
  * into a CUDA graph on the context stream and every call launches that graph
  * (same kernels, same order); a stream that cannot be captured runs them
- * directly. */
+ * directly.  BFC_ETIMEOUT if a bounded device wait (the tensor-core Gram's
+ * mbarriers, the bulk copies of the solve) expired; the sweep's results are
+ * then undefined and the context stays usable. */
 bfc_status bfc_als_sweep(bfc_ctx* ctx, bfc_sweep_stats* out);
 
 /* Gradient of f with respect to all parameters (Eqs. (grad_butterfly_1),
