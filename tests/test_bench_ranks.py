@@ -72,3 +72,24 @@ def test_kernel_rooflines_arithmetic():
     assert solve["refine_steps_per_slice"] == pytest.approx(1.0)
     assert solve["bytes"] == S * (2080 + 64) * 8 + nnz * (16 * 8 + 4) + S * 64 * 24 + 4 * (S + 1)
     assert "k_eval" in rows and rows["k_eval"]["launch_ms"] == pytest.approx(0.25)
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` times the oracle on the host cores and
+    prints one JSON line with the arm's contract: the same metric and unit as
+    the GPU arm, a cpu_baseline describing the run, and an e2e entry that
+    moves no bytes between host and device."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=600,
+                         cwd=root, check=True).stdout
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
