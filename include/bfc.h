@@ -344,27 +344,45 @@ bfc_status bfc_profile_read(bfc_ctx* ctx, bfc_kernel_profile* out, int32_t cap,
  * allocating library routine.
  *
  * Computes, for the butterfly with packed complex128 factors `factors` (the
- * layout above, sizes n = b 2^L and rank r in [1, 10]), over m entries:
- *     sums[0] = sum_e |t_e - x_{i_e j_e}|^2,   sums[1] = sum_e |t_e|^2
- * (the two sums of Eq. (BF_convergence)), with FP64 entry evaluation.  All
- * of factors, i, j, t (m interleaved complex128) and sums (2 doubles) are
- * DEVICE pointers owned by the caller.  The work is enqueued on `stream` (a
- * cudaStream_t, NULL = default stream) and the call returns without waiting;
- * sums is valid once the stream reaches this point.
+ * layout above, sizes n = b 2^L and rank r in [1, 10]), over m entries the
+ * squared residual norm and the squared data norm:
+ *     sums[0] = sum_e |t_e - x_{i_e j_e}|^2,   sums[1] = sum_e |t_e|^2,
+ * with FP64 entry evaluation.  All of factors, i, j, t (m interleaved
+ * complex128) and sums (2 doubles) are DEVICE pointers owned by the caller:
+ * device (or managed) memory usable on the current device, with factors and
+ * t 16-byte aligned (they are read as 16-byte vectors), i and j 4-byte and
+ * sums 8-byte aligned.  The work is enqueued on `stream` (a cudaStream_t,
+ * NULL = default stream) and the call returns without waiting; sums is
+ * valid once the stream reaches this point.
  * Scratch: per-block partial sums live in one fixed file-scope device array
  * of the library (256 KiB, held by every GPU that loads the library until the
- * process exits), so m may be at most 4,194,304; larger m, bad sizes or NULL
- * pointers return BFC_EINVAL (message in bfc_last_error(NULL)) without
- * launching anything.  An index outside [0, n) makes both sums NaN.
+ * process exits), so m may be at most 4,194,304; larger m, bad sizes, NULL,
+ * misaligned or host pointers return BFC_EINVAL (message in
+ * bfc_last_error(NULL)) without launching anything.  m = 0 sets both sums
+ * to 0.  An index outside [0, n) makes both sums NaN.
  * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  Every call shares the array and leaves its partials
- * in it (the bad-index flag is cleared at the start of each call): calls that
+ * (cudaGetSymbolAddress) with the device current and keeps it; make that
+ * first call before any stream capture, and do not use the library across a
+ * cudaDeviceReset.  Every call shares the array and leaves its partials in it
+ * (the bad-index flag is cleared at the start of each call): calls that
  * overlap on the GPU, on any streams, race and give wrong sums. */
 bfc_status bfc_residual_noalloc(int64_t n, int32_t L, int32_t b, int32_t r,
                                 const double* factors, int64_t m, const int32_t* i,
                                 const int32_t* j, const double* t, double* sums,
                                 void* stream);
+
+/* Failure injection for tests of the error paths; the paper has no
+ * counterpart.  Nothing faults on the GPU: kind 1 makes the kernels of this
+ * context skip issuing the bulk copies of the middle-level solve and
+ * gradient (the precision form at even rank) while still waiting for them,
+ * with a wait limit of a few tries; the waits expire, the kernels load that
+ * data by plain loads instead, and bfc_als_sweep / bfc_grad return
+ * BFC_ETIMEOUT.  Kind 2 raises the context's device error word from the host
+ * before the status read, with the same result on any path.  Kind 0 turns
+ * injection off.  The setting stays until changed; the context stays usable
+ * and its results are valid again once injection is off.  EINVAL for another
+ * kind. */
+bfc_status bfc_inject_fault(bfc_ctx* ctx, int32_t kind);
 
 /* Message for the last failed call on ctx (or of the last failed
  * bfc_create when ctx is NULL).  Never NULL. */

@@ -29,7 +29,7 @@ __all__ = [
     "batch_complete", "GRAM_TENSOR", "GRAM_CUDA",
     "bfc_mlp_create", "bfc_mlp_dims", "bfc_mlp_num_params", "bfc_mlp_get_params", "bfc_mlp_set_params",
     "bfc_mlp_set_scaling", "bfc_mlp_forward", "bfc_mlp_grad", "bfc_mlp_train", "bfc_mlp_destroy",
-    "bfc_init_learned", "bfc_canonicalize", "Mlp", "bfc_measure_alu_peaks",
+    "bfc_init_learned", "bfc_canonicalize", "Mlp", "bfc_measure_alu_peaks", "bfc_inject_fault",
 ]
 
 PREC_FP64 = 0
@@ -46,7 +46,7 @@ exported_symbols = (
     "bfc_batch_complete", "bfc_decode", "bfc_get_order", "bfc_residual_noalloc",
     "bfc_mlp_create", "bfc_mlp_dims", "bfc_mlp_num_params", "bfc_mlp_get_params", "bfc_mlp_set_params",
     "bfc_mlp_set_scaling", "bfc_mlp_forward", "bfc_mlp_grad", "bfc_mlp_train", "bfc_mlp_destroy",
-    "bfc_init_learned", "bfc_canonicalize", "bfc_measure_alu_peaks",
+    "bfc_init_learned", "bfc_canonicalize", "bfc_measure_alu_peaks", "bfc_inject_fault",
     "bfc_profile_enable", "bfc_profile_read", "bfc_last_error", "bfc_destroy",
 )
 
@@ -163,6 +163,8 @@ def load():
         lib.bfc_get_order.restype = i32
         lib.bfc_residual_noalloc.argtypes = [i64, i32, i32, i32, vp, i64, vp, vp, vp, vp, vp]
         lib.bfc_residual_noalloc.restype = i32
+        lib.bfc_inject_fault.argtypes = [vp, i32]
+        lib.bfc_inject_fault.restype = i32
         lib.bfc_profile_enable.argtypes = [vp, i32]
         lib.bfc_profile_enable.restype = i32
         lib.bfc_profile_read.argtypes = [vp, ctypes.POINTER(KernelProfile), i32, ctypes.POINTER(i32)]
@@ -403,13 +405,41 @@ def bfc_get_order(ctx, level: int, N: int, K: int):
     return perm, seg
 
 
+def _check_cuda_tensor(x, what, dtype_name, numel=None, min_numel=None):
+    if not hasattr(x, "is_cuda") or not x.is_cuda:
+        raise BfcError(1, f"{what} must be a CUDA tensor")
+    if str(x.dtype) != "torch." + dtype_name:
+        raise BfcError(1, f"{what} must have dtype {dtype_name}, not {x.dtype}")
+    if not x.is_contiguous():
+        raise BfcError(1, f"{what} must be contiguous")
+    if numel is not None and x.numel() != numel:
+        raise BfcError(1, f"{what} has {x.numel()} elements, expected {numel}")
+    if min_numel is not None and x.numel() < min_numel:
+        raise BfcError(1, f"{what} has {x.numel()} elements, expected at least {min_numel}")
+
+
 def bfc_residual_noalloc(n: int, L: int, b: int, r: int, factors, i, j, t, sums, stream=None):
     """Allocation-free residual sums on caller-owned device buffers (torch
     CUDA tensors): sums[0] = sum |t - x|^2, sums[1] = sum |t|^2.  Enqueued on
-    `stream` (a raw cudaStream_t handle, None = default stream); no wait."""
+    `stream` (a raw cudaStream_t handle, None = default stream); no wait.
+    factors: float64, 2 * bfc_num_params values; i, j: int32, m each; t:
+    float64, 2 m values; sums: float64, at least 2 values."""
     m = int(i.shape[0])
+    _check_cuda_tensor(i, "i", "int32")
+    _check_cuda_tensor(j, "j", "int32", numel=m)
+    _check_cuda_tensor(t, "t", "float64", numel=2 * m)
+    _check_cuda_tensor(sums, "sums", "float64", min_numel=2)
+    P = bfc_num_params(n, L, b, r)
+    if P > 0:
+        _check_cuda_tensor(factors, "factors", "float64", numel=2 * P)
     _check(load().bfc_residual_noalloc(n, L, b, r, _ptr(factors), m, _ptr(i), _ptr(j), _ptr(t),
                                        _ptr(sums), ctypes.c_void_p(stream or 0)), None)
+
+
+def bfc_inject_fault(ctx, kind: int):
+    """Test-only failure injection (0 off, 1 skipped bulk copies with expiring
+    bounded waits, 2 device error word raised from the host)."""
+    _check(load().bfc_inject_fault(ctx, int(kind)), ctx)
 
 
 def bfc_profile_enable(ctx, enable: bool):

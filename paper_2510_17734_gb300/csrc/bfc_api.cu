@@ -348,10 +348,21 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
 
 // ---------------------------------------------------------------- sweeps
 
+// Failure injection of the tests, kind 2: the device error word is raised
+// from the host, as if a bounded device wait had expired.
+static bfc_status inject_error_word(Ctx* c)
+{
+    if (c->inject != 2) return BFC_OK;
+    static const unsigned long long one = 1ull;
+    BFC_CK(c, cudaMemcpyAsync(c->d_count + 5, &one, sizeof(one), cudaMemcpyHostToDevice, c->stream));
+    return BFC_OK;
+}
+
 static bfc_status collect_stats(Ctx* c, bfc_sweep_stats* out, float ms)
 {
     double hs[8];
     unsigned long long hc[6];
+    BFC_TRY(inject_error_word(c));
     BFC_CK(c, cudaMemcpyAsync(hs, c->d_scalars, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     BFC_CK(c, cudaMemcpyAsync(hc, c->d_count, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
     BFC_TRY(sync(c));
@@ -497,6 +508,7 @@ static bfc_status grad_into(Ctx* c, int include_reg, double2* G, double* hs)
     BFC_TRY(factor_sumsq(c, 2));
     if (include_reg) launch_axpy((double*)G, (const double*)c->z1d, c->P.lambda, 2 * c->Pn, c->stream);
     BFC_LAUNCH_CHECK(c, "grad tail");
+    BFC_TRY(inject_error_word(c));
     unsigned long long terr = 0;
     BFC_CK(c, cudaMemcpyAsync(hs, c->d_scalars, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     BFC_CK(c, cudaMemcpyAsync(&terr, c->d_count + 5, sizeof(terr), cudaMemcpyDeviceToHost, c->stream));
@@ -1210,6 +1222,17 @@ bfc_status bfc_profile_read(bfc_ctx* ctx, bfc_kernel_profile* out, int32_t cap, 
         out[q].launches = c->prof_rec[q].launches;
         out[q].total_ms = c->prof_rec[q].total_ms;
     }
+    return BFC_OK;
+}
+
+bfc_status bfc_inject_fault(bfc_ctx* ctx, int32_t kind)
+{
+    if (!ctx) return fail(nullptr, BFC_EINVAL, "null context");
+    Ctx* c = (Ctx*)ctx;
+    if (kind < 0 || kind > 2) return fail(c, BFC_EINVAL, "fault kind must be 0, 1 or 2");
+    BFC_CK(c, cudaStreamSynchronize(c->stream));
+    c->inject = kind;
+    drop_graph(c);   // the captured sweep holds the kernels' arguments
     return BFC_OK;
 }
 

@@ -88,6 +88,11 @@ struct Ctx {
     int64_t graph_launches = 0;     // kernels in the captured sweep
     bool graph_tc = false;          // Gram kernel the capture used
 
+    // failure injection of the tests (bfc_inject_fault): 0 off, 1 bulk copies
+    // of the solve and gradient kernels not issued (their bounded waits
+    // expire), 2 the device error word set on the host before the status read
+    int32_t inject = 0;
+
     // profiling
     bool prof = false;
     int64_t n_launch = 0;           // kernels launched by this context so far

@@ -56,12 +56,14 @@ template <typename V> __device__ __forceinline__ V from_d2(double2 a)
     return v;
 }
 
-// Kahan step: s + x with running compensation c (true sum ~ s - c).
+// Kahan step: s + x with running compensation c (true sum ~ s - c).  The
+// steps are explicitly rounded so that no product of the caller's x can be
+// contracted into them.
 __device__ __forceinline__ void kahan(float& s, float& c, float x)
 {
-    float y = x - c;
-    float t = s + y;
-    c = (t - s) - y;
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
     s = t;
 }
 
@@ -195,25 +197,30 @@ template <typename E> __device__ __forceinline__ void csub_mul_conj(E& acc, E a,
 
 // Error-free transformations (Knuth TwoSum, FMA-based TwoProd) for
 // double-float ("hi + lo" float pair, about 48 significant bits) arithmetic
-// on the FP32 pipes.
+// on the FP32 pipes.  Every operation whose rounding the transformation
+// relies on is an explicitly rounded intrinsic (__fadd_rn, __fsub_rn,
+// __fmul_rn): nvcc contracts a plain product feeding an addition into one
+// FMA by default (--fmad=true), which would make s = a + b exact in the
+// product and leave e counting the product's rounding error twice.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 // acc -= k * (sh + sl) for complex k (float) and a double-float complex s;
-// acc = {re_hi, re_lo, im_hi, im_lo}.
+// acc = {re_hi, re_lo, im_hi, im_lo}.  p = fl(k sh) and e = k sh - p exactly
+// (TwoProd by FMA); the lo-part products only need ordinary accuracy.
 __device__ __forceinline__ void df_sub_cmul(float4& acc, float2 k, float2 sh, float2 sl)
 {
     float t, e;
-    const float p1 = k.x * sh.x, e1 = fmaf(k.x, sh.x, -p1);
-    const float p2 = k.y * sh.y, e2 = fmaf(k.y, sh.y, -p2);
+    const float p1 = __fmul_rn(k.x, sh.x), e1 = fmaf(k.x, sh.x, -p1);
+    const float p2 = __fmul_rn(k.y, sh.y), e2 = fmaf(k.y, sh.y, -p2);
     two_sum(acc.x, -p1, t, e); acc.x = t; acc.y += e;
     two_sum(acc.x, p2, t, e); acc.x = t; acc.y += e;
     acc.y -= e1 - e2 + (k.x * sl.x - k.y * sl.y);
-    const float p3 = k.x * sh.y, e3 = fmaf(k.x, sh.y, -p3);
-    const float p4 = k.y * sh.x, e4 = fmaf(k.y, sh.x, -p4);
+    const float p3 = __fmul_rn(k.x, sh.y), e3 = fmaf(k.x, sh.y, -p3);
+    const float p4 = __fmul_rn(k.y, sh.x), e4 = fmaf(k.y, sh.x, -p4);
     two_sum(acc.z, -p3, t, e); acc.z = t; acc.w += e;
     two_sum(acc.z, -p4, t, e); acc.z = t; acc.w += e;
     acc.w -= e3 + e4 + (k.x * sl.y + k.y * sl.x);
@@ -984,10 +991,12 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
             typename cvec<T>::type* __restrict__ Zt, double2* __restrict__ fb, double lambda_in, double ridge,
             unsigned long long* __restrict__ nsing, unsigned long long* __restrict__ nfb,
             unsigned long long* __restrict__ nsteps, int32_t* __restrict__ fblist, int S,
-            unsigned long long* __restrict__ terr)
+            unsigned long long* __restrict__ terr, int skip_copy)
 {
     // nfb: slices handed to the FP64 fallback (length of fblist); nsteps: refinement steps;
-    // terr: raised when the bulk copy of a record does not complete within the wait limit
+    // terr: raised when the bulk copy of a record does not complete within the wait limit;
+    // skip_copy (failure injection of the tests, bfc_inject_fault): the bulk copies are not
+    // issued and the waits give up after a few tries
     typedef typename cvec<T>::type V;
     typedef SolveCfg<T, R> C;
     constexpr int D = C::D, NPK = C::NPK, NS = C::NS;
@@ -1005,6 +1014,12 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
     constexpr uint32_t KBULK = (uint32_t)((NPK & ~1) * sizeof(V));   // a multiple of 16 bytes
     constexpr bool BULK = C::MIXED && KBULK >= 16;
     uint32_t phase = 0;
+    // warp-uniform: bulk copies still in use (cleared for good when a wait
+    // expires); pending: a copy that was issued and then given up on
+    bool use_bulk = BULK;
+    bool pending = false;
+    uint32_t pending_phase = 0;
+    const uint32_t wait_limit = skip_copy ? 64u : (1u << 22);
     if constexpr (BULK) {
         if (lane == 0) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
@@ -1016,41 +1031,58 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
     for (int k = blockIdx.x * C::WPB + wib; k < S; k += gridDim.x * C::WPB) {
         const V* K = rec + (size_t)k * (NPK + D);
         __syncwarp();
+        bool have = false;
         if constexpr (BULK) {
-            // the record stride D (D + 3) / 2 is even for D = r^2, so every
-            // record starts on a 16-byte boundary; the previous slice's
-            // accesses to the factor area are ordered before the copy
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) {
-                asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
-                             ::"r"(bar), "r"(KBULK) : "memory");
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             ::"r"((uint32_t)__cvta_generic_to_shared(Lm)), "l"(K), "r"(KBULK), "r"(bar)
-                             : "memory");
+            if (use_bulk) {
+                // the record stride D (D + 3) / 2 is even for D = r^2, so every
+                // record starts on a 16-byte boundary; the previous slice's
+                // accesses to the factor area are ordered before the copy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
+                                 ::"r"(bar), "r"(KBULK) : "memory");
+                    if (!skip_copy)
+                        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                     ::"r"((uint32_t)__cvta_generic_to_shared(Lm)), "l"(K), "r"(KBULK), "r"(bar)
+                                     : "memory");
+                }
+                if ((NPK & 1) && lane == 0) Lm[NPK - 1] = K[NPK - 1];
+                bool done = false;
+                for (uint32_t it = 0; it < wait_limit && !done; ++it) {
+                    uint32_t ok;
+                    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n"
+                                 "selp.u32 %0, 1, 0, p;\n}\n"
+                                 : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
+                    done = ok != 0;
+                }
+                // the phase completes once for all lanes: any lane that saw it
+                // completed makes the copy valid for the warp
+                done = __any_sync(0xffffffffu, done);
+                if (done) {
+                    have = true;
+                } else {
+                    // the copy did not complete: report it, issue no further
+                    // copies on this barrier and load by plain loads from here
+                    // on (the call's results are undefined)
+                    if (lane == 0) atomicExch(terr, 1ull);
+                    use_bulk = false;
+                    pending = !skip_copy;
+                    pending_phase = phase;
+                }
+                phase ^= 1u;
             }
-            if ((NPK & 1) && lane == 0) Lm[NPK - 1] = K[NPK - 1];
-            bool done = false;
-            for (uint32_t it = 0; it < (1u << 22) && !done; ++it) {
-                uint32_t ok;
-                asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n"
-                             "selp.u32 %0, 1, 0, p;\n}\n"
-                             : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
-                done = ok != 0;
-            }
-            phase ^= 1u;
-            if (!done) {
-                // the copy did not complete: report it; the slice's results are undefined
-                if (lane == 0) atomicExch(terr, 1ull);
-            }
-        } else if constexpr (C::MIXED) {
-            const float4* src = reinterpret_cast<const float4*>(K);
-            float4* dst = reinterpret_cast<float4*>(Lm);
+        }
+        if (!have) {
+            if constexpr (C::MIXED) {
+                const float4* src = reinterpret_cast<const float4*>(K);
+                float4* dst = reinterpret_cast<float4*>(Lm);
 #pragma unroll 4
-            for (int q = lane; q < NPK / 2; q += 32) dst[q] = src[q];
-            if ((NPK & 1) && lane == 0) Lm[NPK - 1] = K[NPK - 1];
-        } else {
-            for (int q = lane; q < NPK; q += 32) Lm[q] = K[q];
+                for (int q = lane; q < NPK / 2; q += 32) dst[q] = src[q];
+                if ((NPK & 1) && lane == 0) Lm[NPK - 1] = K[NPK - 1];
+            } else {
+                for (int q = lane; q < NPK; q += 32) Lm[q] = K[q];
+            }
         }
         __syncwarp();
         double tr = 0.0;
@@ -1246,6 +1278,17 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
         __syncwarp();
         // left environment update into the next order
         slice_h_update<T, R>(H, zt_s, nxt, Hn, seg[k], seg[k + 1], lane);
+    }
+    if (pending) {
+        // a copy that was given up on may still land: wait for it (bounded)
+        // before the warp's shared memory is released
+        for (uint32_t it = 0; it < (1u << 22); ++it) {
+            uint32_t ok;
+            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n"
+                         "selp.u32 %0, 1, 0, p;\n}\n"
+                         : "=r"(ok) : "r"(bar), "r"(pending_phase) : "memory");
+            if (ok) break;
+        }
     }
 }
 
@@ -1547,7 +1590,7 @@ k_grad_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
            const typename cvec<T>::type* __restrict__ Rc, const int32_t* __restrict__ seg,
            const int32_t* __restrict__ nxt, const typename cvec<T>::type* __restrict__ Zt,
            typename cvec<T>::type* __restrict__ Hn, typename cvec<T>::type* __restrict__ Rn,
-           double2* __restrict__ Gm, int S, unsigned long long* __restrict__ terr)
+           double2* __restrict__ Gm, int S, unsigned long long* __restrict__ terr, int skip_copy)
 {
     typedef typename cvec<T>::type V;
     constexpr int D = R * R;
@@ -1562,13 +1605,20 @@ k_grad_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
     __shared__ double2 g_s[NG == 2 ? 64 : 1];
     // complex64 at even rank: a chunk's h and w rows (contiguous, 16-byte
     // multiples) arrive by two bulk copies counted on one mbarrier (the wait
-    // is bounded; on expiry *terr is raised and the results are undefined)
+    // is bounded; on expiry *terr is raised, the results are undefined, and
+    // the CTA issues no further copies: it loads by plain loads from then on).
+    // skip_copy (failure injection of the tests, bfc_inject_fault): the copies
+    // are not issued and the waits give up after a few tries.
     __shared__ __align__(8) unsigned long long cbar;
     const int tid = threadIdx.x;
     const int grp = NG == 2 ? tid >> 6 : 0;
     const int q0 = NG == 2 ? (tid & 63) : tid;
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&cbar);
     uint32_t phase = 0;
+    bool use_bulk = VEC;          // CTA-uniform
+    bool pending = false;         // copies issued and then given up on
+    uint32_t pending_phase = 0;
+    const uint32_t wait_limit = skip_copy ? 64u : (1u << 22);
     if constexpr (VEC) {
         if (tid == 0) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
@@ -1585,34 +1635,50 @@ k_grad_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
         for (int u = 0; u < NQ; ++u) g[u] = make_double2(0.0, 0.0);
         for (int base = s0; base < s1; base += CH) {
             const int cnt = min(CH, s1 - base);
+            bool have = false;
             if constexpr (VEC) {
-                // every thread's reads of the previous chunk are ordered
-                // before the copy engine overwrites the buffers
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncthreads();
-                if (tid == 0) {
-                    const uint32_t bytes = (uint32_t)(cnt * R * sizeof(V));
-                    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
-                                 ::"r"(bar), "r"(2 * bytes) : "memory");
-                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                                 ::"r"((uint32_t)__cvta_generic_to_shared(h_s)), "l"(H + (size_t)base * R), "r"(bytes),
-                                 "r"(bar) : "memory");
-                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                                 ::"r"((uint32_t)__cvta_generic_to_shared(w_s)), "l"(Wm + (size_t)base * R), "r"(bytes),
-                                 "r"(bar) : "memory");
+                if (use_bulk) {
+                    // every thread's reads of the previous chunk are ordered
+                    // before the copy engine overwrites the buffers
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncthreads();
+                    if (tid == 0) {
+                        const uint32_t bytes = (uint32_t)(cnt * R * sizeof(V));
+                        asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n"
+                                     ::"r"(bar), "r"(2 * bytes) : "memory");
+                        if (!skip_copy) {
+                            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                         ::"r"((uint32_t)__cvta_generic_to_shared(h_s)), "l"(H + (size_t)base * R),
+                                         "r"(bytes), "r"(bar) : "memory");
+                            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                         ::"r"((uint32_t)__cvta_generic_to_shared(w_s)), "l"(Wm + (size_t)base * R),
+                                         "r"(bytes), "r"(bar) : "memory");
+                        }
+                    }
+                    for (int x = tid; x < cnt; x += blockDim.x) r_s[x] = Rc[base + x];
+                    bool done = false;
+                    for (uint32_t it = 0; it < wait_limit && !done; ++it) {
+                        uint32_t ok;
+                        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n"
+                                     "selp.u32 %0, 1, 0, p;\n}\n"
+                                     : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
+                        done = ok != 0;
+                    }
+                    // the phase completes once for every thread: any thread
+                    // that saw it complete makes the chunk valid for the CTA
+                    done = __syncthreads_or(done) != 0;
+                    if (done) {
+                        have = true;
+                    } else {
+                        if (tid == 0) atomicExch(terr, 1ull);
+                        use_bulk = false;
+                        pending = !skip_copy;
+                        pending_phase = phase;
+                    }
+                    phase ^= 1u;
                 }
-                for (int x = tid; x < cnt; x += blockDim.x) r_s[x] = Rc[base + x];
-                bool done = false;
-                for (uint32_t it = 0; it < (1u << 22) && !done; ++it) {
-                    uint32_t ok;
-                    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n"
-                                 "selp.u32 %0, 1, 0, p;\n}\n"
-                                 : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
-                    done = ok != 0;
-                }
-                phase ^= 1u;
-                if (!done && tid == 0) atomicExch(terr, 1ull);
-            } else {
+            }
+            if (!have) {
                 __syncthreads();
                 for (int x = tid; x < cnt * R; x += blockDim.x) {
                     h_s[x] = H[(size_t)base * R + x];
@@ -1688,6 +1754,17 @@ k_grad_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
                 const int q = q0 + 128 * u;
                 if (q < D) Gm[(size_t)k * D + q] = g[u];
             }
+        }
+    }
+    if (pending) {
+        // copies that were given up on may still land: wait for them
+        // (bounded) before the CTA's shared memory is released
+        for (uint32_t it = 0; it < (1u << 22); ++it) {
+            uint32_t ok;
+            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n"
+                         "selp.u32 %0, 1, 0, p;\n}\n"
+                         : "=r"(ok) : "r"(bar), "r"(pending_phase) : "memory");
+            if (ok) break;
         }
     }
 }

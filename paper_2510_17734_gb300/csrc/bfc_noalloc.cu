@@ -86,7 +86,9 @@ __global__ void __launch_bounds__(256) k_residual_final_noalloc(const double* __
 __global__ void k_residual_clear_noalloc(double* __restrict__ scratch) { scratch[2 * NOALLOC_MAX_BLOCKS] = 0.0; }
 
 // Device address of the scratch array, looked up once per device (with that
-// device current) on the first call made there.
+// device current) on the first call made there.  The cached address is that
+// of the device's current context: the library must not be used across a
+// cudaDeviceReset (a new primary context reloads the module elsewhere).
 static std::mutex g_noalloc_mu;
 static double* g_noalloc_ptr[128];
 
@@ -105,6 +107,29 @@ static bfc_status noalloc_scratch(double** out)
         g_noalloc_ptr[dev] = (double*)p;
     }
     *out = g_noalloc_ptr[dev];
+    return BFC_OK;
+}
+
+// EINVAL unless p is device or managed memory usable on the current device
+// and `align`-byte aligned (cudaPointerGetAttributes allocates nothing).
+static bfc_status check_device_ptr(const void* p, size_t align, const char* what)
+{
+    if ((uintptr_t)p % align != 0)
+        return fail(nullptr, BFC_EINVAL, std::string(what) + " is not " + std::to_string(align) + "-byte aligned");
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, BFC_EINVAL, std::string(what) + ": not a CUDA pointer (" + cudaGetErrorString(e) + ")");
+    }
+    int dev = -1;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, BFC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (a.type == cudaMemoryTypeManaged) return BFC_OK;
+    if (a.type != cudaMemoryTypeDevice)
+        return fail(nullptr, BFC_EINVAL, std::string(what) + " is not device memory");
+    if (a.device != dev)
+        return fail(nullptr, BFC_EINVAL, std::string(what) + " is memory of another device");
     return BFC_OK;
 }
 
@@ -139,6 +164,16 @@ extern "C" bfc_status bfc_residual_noalloc(int64_t n, int32_t L, int32_t b, int3
                     "m = " + std::to_string(m) + " is outside [0, " + std::to_string(NOALLOC_MAX_ENTRIES) +
                         "], the capacity of the fixed scratch of bfc_residual_noalloc");
     if (!sums || (m > 0 && (!factors || !i || !j || !t))) return fail(nullptr, BFC_EINVAL, "null argument");
+    // every pointer must be device (or managed) memory of the current device
+    // and aligned for the kernels' vector loads: complex128 values are read
+    // as 16-byte double2, indices as int32, sums written as doubles
+    BFC_TRY(check_device_ptr(sums, 8, "sums"));
+    if (m > 0) {
+        BFC_TRY(check_device_ptr(factors, 16, "factors"));
+        BFC_TRY(check_device_ptr(t, 16, "t"));
+        BFC_TRY(check_device_ptr(i, 4, "i"));
+        BFC_TRY(check_device_ptr(j, 4, "j"));
+    }
     cudaStream_t st = (cudaStream_t)stream;
     double* scratch = nullptr;
     BFC_TRY(noalloc_scratch(&scratch));

@@ -139,7 +139,7 @@ template <typename T, int R> struct Path {
                 k_mid_solve<T, R><<<gsolve, 32 * SC::WPB, SC::SMEM, c->stream>>>(
                     (const V*)c->rec, hin, c->seg[m], c->nxt[m], hout, c->Zd + (size_t)(m - 1) * S * R * R,
                     (V*)c->Zt + (size_t)(m - 1) * S * R * R, c->fb, c->P.lambda, c->ridge, c->d_count,
-                    c->d_count + 3, c->d_count + 2, c->fblist, (int)S, c->d_count + 5);
+                    c->d_count + 3, c->d_count + 2, c->fblist, (int)S, c->d_count + 5, c->inject == 1 ? 1 : 0);
             }
             if (SC::MIXED) {
                 ProfScope ps(c, "mid_fallback", 2);
@@ -187,7 +187,7 @@ template <typename T, int R> struct Path {
             k_grad_mid<T, R><<<g, 128, 0, c->stream>>>(Hb[in], W + (size_t)m * NR, Rb[in], c->seg[m], c->nxt[m],
                                                         (const V*)c->Zt + (size_t)(m - 1) * S * R * R, Hb[out],
                                                         Rb[out], GZ + (size_t)(m - 1) * S * R * R, (int)S,
-                                                        c->d_count + 5);
+                                                        c->d_count + 5, c->inject == 1 ? 1 : 0);
         }
         BFC_LAUNCH_CHECK(c, "grad_mid");
         {
