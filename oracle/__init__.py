@@ -21,6 +21,13 @@ Functions and the passage each follows:
                            Sec. 4.2)
   lbfgs                    gradient completion of f by limited-memory BFGS
                            (Nocedal and Wright, Alg. 7.4) over grad()
+  matvec                   X(S) V by the definition u_i = sum_j x_ij v_j (the
+                           product Eq. (butterfly-mat-vec) forms by
+                           contractions)
+  set_threads, threads     the threaded variant: OpenMP over independent
+                           systems and entries, bit-identical to serial
+Modules: first_order (Alg. 3/4 ADAM, Alg. 5 ADF, App. A.3 sweeps), lr2bf
+(Alg. 2), gauge (left orthogonalization), mlp (the learned start's network).
 """
 from __future__ import annotations
 
@@ -49,7 +56,11 @@ def build(force: bool = False) -> str:
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
            "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP for the threaded variant (same arithmetic per system; see
+    # set_threads); a compiler without it builds the serial oracle
+    res = subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True, text=True)
+    if res.returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -88,8 +99,40 @@ def _load():
         lib.bfo_grad.restype = None
         lib.bfo_embed_lowrank.argtypes = [i64, i32, i32, i32, i32, vp, vp, vp, vp]
         lib.bfo_embed_lowrank.restype = None
+        lib.bfo_matvec.argtypes = [i64, i32, i32, i32, vp, i32, vp, vp]
+        lib.bfo_matvec.restype = None
+        lib.bfo_set_threads.argtypes = [i32]
+        lib.bfo_set_threads.restype = None
+        lib.bfo_max_threads.argtypes = []
+        lib.bfo_max_threads.restype = i32
         _lib = lib
         return lib
+
+
+def set_threads(threads: int) -> None:
+    """Threads of the oracle's parallel loops (independent systems and
+    entries; every sum keeps its serial order, so results are bit-identical
+    for any thread count).  1 = serial (the default)."""
+    _load().bfo_set_threads(int(threads))
+
+
+def max_threads() -> int:
+    """Threads OpenMP would use by default (1 if built without OpenMP)."""
+    return int(_load().bfo_max_threads())
+
+
+class threads:
+    """Context manager: run the oracle on `count` threads inside the block."""
+
+    def __init__(self, count: int):
+        self.count = count
+
+    def __enter__(self):
+        set_threads(self.count)
+        return self
+
+    def __exit__(self, *exc):
+        set_threads(1)
 
 
 def _i32(a):
@@ -179,6 +222,18 @@ def embed_lowrank(n, L, b, r, A, B, pad=None):
     return out
 
 
+def matvec(n, L, b, r, packed, V):
+    """U = X(S) V by the definition u_i = sum_j x_ij v_j (V: n or n x nvec
+    complex128)."""
+    packed = _c128(packed)
+    V = _c128(V)
+    one = V.ndim == 1
+    Vm = np.ascontiguousarray(V.reshape(n, -1))
+    U = np.zeros_like(Vm)
+    _load().bfo_matvec(n, L, b, r, _ptr(packed), Vm.shape[1], _ptr(Vm), _ptr(U))
+    return U.ravel() if one else U
+
+
 def lr_complete(n, R, lam, A0, B0, i, j, t, sweeps):
     """Low-rank matrix completion = Alg. 1 with L = 0 (leaf size n).
     Returns (A, B) with X = A B^T."""
@@ -188,13 +243,15 @@ def lr_complete(n, R, lam, A0, B0, i, j, t, sweeps):
     return packed[:n * R].reshape(n, R), packed[n * R:].reshape(n, R)
 
 
-def lbfgs(n, L, b, r, lam, packed, i, j, t, iters, memory=10, c1=1e-4):
+def lbfgs(n, L, b, r, lam, packed, i, j, t, iters, memory=10, c1=1e-4, trace=None):
     """Limited-memory BFGS on the 2P real parameters (Re, Im interleaved) of
     f = 1/2 sum |x - t|^2 + lambda/2 ||S||^2, gradients from grad().
     Two-loop recursion, H0 = gamma I with gamma = s^T y / y^T y of the newest
     pair; backtracking Armijo line search (c1, halving, <= 30 trials) from
     step 1, or 1/||g|| before the first pair; a pair is kept only if
-    s^T y > 1e-12 ||s|| ||y||.  Returns (final packed factors, objectives)."""
+    s^T y > 1e-12 ||s|| ||y||.  Returns (final packed factors, objectives).
+    `trace` (a list) receives per iteration (x, g, d, step, f) before the
+    step, for the tests that check the direction against the BFGS matrix."""
     def fg(xr):
         g, f = grad(n, L, b, r, lam, xr.view(np.complex128), i, j, t, include_reg=True)
         return f, g.view(np.float64).copy()
@@ -225,6 +282,8 @@ def lbfgs(n, L, b, r, lam, packed, i, j, t, iters, memory=10, c1=1e-4):
             if ft <= f + c1 * step * gtd:
                 break
             step *= 0.5
+        if trace is not None:
+            trace.append((x.copy(), g.copy(), d.copy(), step, f))
         s_, y_ = xt - x, gt - g
         sy = float(s_ @ y_)
         if sy > 1e-12 * float(np.linalg.norm(s_)) * float(np.linalg.norm(y_)):

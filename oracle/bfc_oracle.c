@@ -8,8 +8,11 @@
  * leg of the benchmark may load it.  It shares no code, header, table or
  * helper with the CUDA library; the two only see the same seeded inputs.
  *
- * Everything is complex128 (C99 `double complex`), serial, with sums taken
- * in the natural order of the entries (stable by slice, then by draw order).
+ * Everything is complex128 (C99 `double complex`), with sums taken in the
+ * natural order of the entries (stable by slice, then by draw order).  The
+ * loops over independent systems and entries may run on several threads
+ * (bfo_set_threads); every sum is still taken by one thread in that order, so
+ * the results do not depend on the thread count.
  *
  * Notation (Sec. 3.1, App. A.2):
  *   n = b * 2^L, leaf size b (the paper's c), rank r.
@@ -42,11 +45,31 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
 
 #define BFO_MAX_L 30
 #define BFO_MAX_R 64
+
+/* Threads of the parallel loops (1 = serial).  Only loops whose iterations
+ * are independent systems or entries are parallel, and every sum is taken
+ * by one thread in the serial order, so any thread count gives results
+ * identical bit for bit to the serial ones. */
+static int g_threads = 1;
+
+void bfo_set_threads(int threads) { g_threads = threads < 1 ? 1 : threads; }
+
+int bfo_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ---------------------------------------------------------------- indices */
 
@@ -150,11 +173,21 @@ void bfo_eval(int64_t n, int L, int b, int r, const double* packed, int64_t m,
               const int32_t* ii, const int32_t* jj, double* out)
 {
     bfo_factors F = view(n, L, b, r, (double*)packed);
+#pragma omp parallel for schedule(static) num_threads(g_threads)
     for (int64_t e = 0; e < m; ++e) {
         cplx x = eval_entry(&F, ii[e], jj[e]);
         out[2 * e] = creal(x);
         out[2 * e + 1] = cimag(x);
     }
+}
+
+/* x_e for every entry (in parallel), for the serial sums below. */
+static cplx* eval_all(const bfo_factors* F, int64_t m, const int32_t* ii, const int32_t* jj)
+{
+    cplx* x = (cplx*)malloc((size_t)(m > 0 ? m : 1) * sizeof(cplx));
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+    for (int64_t e = 0; e < m; ++e) x[e] = eval_entry(F, ii[e], jj[e]);
+    return x;
 }
 
 /* Eq. (BF_convergence): ||P_Omega(T - X)||_F / ||P_Omega(T)||_F. */
@@ -163,13 +196,15 @@ double bfo_rel_err(int64_t n, int L, int b, int r, const double* packed,
                    const double* t)
 {
     bfo_factors F = view(n, L, b, r, (double*)packed);
+    cplx* x = eval_all(&F, nnz, ii, jj);
     double num = 0.0, den = 0.0;
     for (int64_t e = 0; e < nnz; ++e) {
         cplx te = t[2 * e] + I * t[2 * e + 1];
-        cplx d = te - eval_entry(&F, ii[e], jj[e]);
+        cplx d = te - x[e];
         num += creal(d * conj(d));
         den += creal(te * conj(te));
     }
+    free(x);
     return den > 0.0 ? sqrt(num / den) : sqrt(num);
 }
 
@@ -180,12 +215,14 @@ double bfo_objective(int64_t n, int L, int b, int r, double lambda,
                      const int32_t* jj, const double* t)
 {
     bfo_factors F = view(n, L, b, r, (double*)packed);
+    cplx* x = eval_all(&F, nnz, ii, jj);
     double fit = 0.0;
     for (int64_t e = 0; e < nnz; ++e) {
         cplx te = t[2 * e] + I * t[2 * e + 1];
-        cplx d = eval_entry(&F, ii[e], jj[e]) - te;
+        cplx d = x[e] - te;
         fit += creal(d * conj(d));
     }
+    free(x);
     double reg = 0.0;
     int64_t P = bfo_num_params(n, L, b, r);
     for (int64_t p = 0; p < 2 * P; ++p) reg += packed[p] * packed[p];
@@ -273,6 +310,52 @@ static int block_solve(const cplx* A, const cplx* tv, int64_t cnt, int d,
     return bad;
 }
 
+/* Solve every block of one factor level: for key k the entries
+ * order[start[k] .. start[k+1]) (stable) form the block.  Outer levels
+ * (level 0: S^1 rows, level L+1: S^{L+2} columns) use the design vector
+ * env_a[e] (length r); middle levels use a_e = env_a[e] (x) env_b[e]
+ * (a[p r + q] = h_p w_q, length r^2).  Block k's solution overwrites
+ * target + k * d.  Blocks are independent (each has its own buffers and its
+ * sums in entry order), so they may run on several threads.  Returns the
+ * number of singular blocks. */
+static int64_t solve_blocks(const bfo_factors* F, int level, const int64_t* order, const int64_t* start,
+                            int64_t K, const cplx* env_a, const cplx* env_b, const cplx* tv_all,
+                            double lambda, cplx* target)
+{
+    const int r = F->r;
+    const int mid = level >= 1 && level <= F->L;
+    const int d = mid ? r * r : r;
+    int64_t maxcnt = 0;
+    for (int64_t k = 0; k < K; ++k)
+        if (start[k + 1] - start[k] > maxcnt) maxcnt = start[k + 1] - start[k];
+    int64_t singular = 0;
+#pragma omp parallel num_threads(g_threads) reduction(+ : singular)
+    {
+        cplx* A = (cplx*)malloc((size_t)(maxcnt > 0 ? maxcnt : 1) * d * sizeof(cplx));
+        cplx* tv = (cplx*)malloc((size_t)(maxcnt > 0 ? maxcnt : 1) * sizeof(cplx));
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t k = 0; k < K; ++k) {
+            int64_t cnt = start[k + 1] - start[k];
+            for (int64_t q = 0; q < cnt; ++q) {
+                int64_t e = order[start[k] + q];
+                if (mid) {
+                    const cplx* he = env_a + e * r;
+                    const cplx* we = env_b + e * r;
+                    for (int p = 0; p < r; ++p)
+                        for (int c = 0; c < r; ++c) A[q * d + p * r + c] = he[p] * we[c];
+                } else {
+                    memcpy(A + q * d, env_a + e * r, (size_t)r * sizeof(cplx));
+                }
+                tv[q] = tv_all[e];
+            }
+            singular += block_solve(A, tv, cnt, d, lambda, target + k * d);
+        }
+        free(A);
+        free(tv);
+    }
+    return singular;
+}
+
 /* ------------------------------------------------------------- ALS sweep */
 
 typedef struct {
@@ -311,10 +394,9 @@ int64_t bfo_als_sweep(int64_t n, int L, int b, int r, double lambda,
     int64_t kmax = (n > S ? n : S);
     int64_t* start = (int64_t*)malloc((size_t)(kmax + 1) * sizeof(int64_t));
     int d2 = r * r;
-    cplx* A = (cplx*)malloc((size_t)N * d2 * sizeof(cplx));
-    cplx* tv = (cplx*)malloc((size_t)N * sizeof(cplx));
 
     /* 1. right environments w[m][e][:] */
+#pragma omp parallel for schedule(static) num_threads(g_threads)
     for (int64_t e = 0; e < N; ++e) {
         cplx* wL = w + ((int64_t)L * N + e) * r;
         for (int c = 0; c < r; ++c) wL[c] = F.zL[(int64_t)jj[e] * r + c];
@@ -333,15 +415,7 @@ int64_t bfo_als_sweep(int64_t n, int L, int b, int r, double lambda,
     /* 2. S^1 fibers, grouped by row i */
     for (int64_t e = 0; e < N; ++e) key[e] = ii[e];
     group_by_key(key, N, n, order, start);
-    for (int64_t i = 0; i < n; ++i) {
-        int64_t cnt = start[i + 1] - start[i];
-        for (int64_t q = 0; q < cnt; ++q) {
-            int64_t e = order[start[i] + q];
-            memcpy(A + q * r, w + e * r, (size_t)r * sizeof(cplx));   /* w_0 */
-            tv[q] = tv_all[e];
-        }
-        singular += block_solve(A, tv, cnt, r, lambda, F.z1 + i * r);
-    }
+    singular += solve_blocks(&F, 0, order, start, n, w, NULL, tv_all, lambda, F.z1);
     for (int64_t e = 0; e < N; ++e)
         memcpy(h + e * r, F.z1 + (int64_t)ii[e] * r, (size_t)r * sizeof(cplx));
 
@@ -349,19 +423,9 @@ int64_t bfo_als_sweep(int64_t n, int L, int b, int r, double lambda,
     for (int m = 1; m <= L; ++m) {
         for (int64_t e = 0; e < N; ++e) key[e] = bfo_slice_id(ii[e], jj[e], m, L, b);
         group_by_key(key, N, S, order, start);
-        for (int64_t k = 0; k < S; ++k) {
-            int64_t cnt = start[k + 1] - start[k];
-            for (int64_t q = 0; q < cnt; ++q) {
-                int64_t e = order[start[k] + q];
-                const cplx* he = h + e * r;
-                const cplx* we = w + ((int64_t)m * N + e) * r;
-                for (int p = 0; p < r; ++p)
-                    for (int c = 0; c < r; ++c) A[q * d2 + p * r + c] = he[p] * we[c];
-                tv[q] = tv_all[e];
-            }
-            cplx* Zk = slice_ptr(&F, m, k);
-            singular += block_solve(A, tv, cnt, d2, lambda, Zk);
-        }
+        singular += solve_blocks(&F, m, order, start, S, h, w + (int64_t)m * N * r, tv_all, lambda,
+                                 slice_ptr(&F, m, 0));
+#pragma omp parallel for schedule(static) num_threads(g_threads)
         for (int64_t e = 0; e < N; ++e) {
             const cplx* Zk = slice_ptr(&F, m, key[e]);
             const cplx* he = h + e * r;
@@ -377,17 +441,10 @@ int64_t bfo_als_sweep(int64_t n, int L, int b, int r, double lambda,
     /* 4. S^{L+2} fibers, grouped by column j, design h_{L+1} */
     for (int64_t e = 0; e < N; ++e) key[e] = jj[e];
     group_by_key(key, N, n, order, start);
-    for (int64_t j = 0; j < n; ++j) {
-        int64_t cnt = start[j + 1] - start[j];
-        for (int64_t q = 0; q < cnt; ++q) {
-            int64_t e = order[start[j] + q];
-            memcpy(A + q * r, h + e * r, (size_t)r * sizeof(cplx));
-            tv[q] = tv_all[e];
-        }
-        singular += block_solve(A, tv, cnt, r, lambda, F.zL + j * r);
-    }
+    singular += solve_blocks(&F, L + 1, order, start, n, h, NULL, tv_all, lambda, F.zL);
 
-    free(w); free(h); free(hn); free(key); free(order); free(start); free(A); free(tv);
+    free(w); free(h); free(hn); free(key); free(order); free(start);
+    (void)d2;
 
     if (st) {
         st->train_rel_err = bfo_rel_err(n, L, b, r, packed, N, ii, jj, t);
@@ -492,4 +549,27 @@ void bfo_embed_lowrank(int64_t n, int L, int b, int r, int R, const double* A,
             for (int a = 0; a < r; ++a)
                 for (int c = 0; c < r; ++c) Zk[a * r + c] = (a == c) ? 1.0 : 0.0;
         }
+}
+
+/* ---------------------------------------------------------------- matvec */
+
+/* u = X(S) V for nvec vectors (Eq. (butterfly-mat-vec) computes the same
+ * product by contractions in O(n log n)); here by its definition,
+ * u_i = sum_j x_ij v_j with every x_ij from Eq. (BF_tensor_rep), O(n^2).
+ * V is n x nvec row-major (V[j * nvec + q]), U likewise; complex128.
+ * Rows are independent and each row sums over j in order. */
+void bfo_matvec(int64_t n, int L, int b, int r, const double* packed, int nvec,
+                const double* V, double* U)
+{
+    bfo_factors F = view(n, L, b, r, (double*)packed);
+    const cplx* Vc = (const cplx*)V;
+    cplx* Uc = (cplx*)U;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(g_threads)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int q = 0; q < nvec; ++q) Uc[i * nvec + q] = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            cplx x = eval_entry(&F, i, j);
+            for (int q = 0; q < nvec; ++q) Uc[i * nvec + q] += x * Vc[j * nvec + q];
+        }
+    }
 }

@@ -109,6 +109,19 @@ def helmholtz_line(n: int, omega: float, h: float, i: np.ndarray, j: np.ndarray)
     return np.exp(1j * omega * rho) / rho
 
 
+def radon_1d(n: int, i: np.ndarray, j: np.ndarray) -> np.ndarray:
+    """The discretized 1-D Radon transform of Sec. 5.3: t = exp(2 pi 1j phi),
+    phi(x, y) = x y + c(x) |y|, c(x) = (2 + sin(2 pi x)) / 8, with
+    x = i' / n and y = j' - n / 2 for the 1-based indices i' = i + 1,
+    j' = j + 1."""
+    x = (np.asarray(i, dtype=np.float64) + 1.0) / n
+    y = (np.asarray(j, dtype=np.float64) + 1.0) - n / 2.0
+    c = (2.0 + np.sin(2.0 * np.pi * x)) / 8.0
+    phi = x * y + c * np.abs(y)
+    # the phase only matters modulo 1: reduce it before the exponential
+    return np.exp(2j * np.pi * (phi - np.floor(phi)))
+
+
 @dataclass
 class Problem:
     """One completion problem: sizes, hyper-parameters and observed data."""
@@ -177,6 +190,42 @@ def config(index: int, n_override: int | None = None) -> Problem:
     return make_problem(f"cfg{index}" + (f"_n{n}" if n_override else ""), n, L, p["b"], p["r"],
                         math.pi * n * p["wfac"], p["h"], n_obs, p["lam"], p["sweeps"],
                         SEED_BASE + 16 * index, noise_rel=p["noise"])
+
+
+RADON_SEED_BASE = 0xBFC20000
+
+
+def radon_problem(n: int = 1024, b: int = 4, r: int = 10, c_obs: float = 30.0, lam: float = 1e-8,
+                  sweeps: int = 20) -> Problem:
+    """The Radon-transform workload of Sec. 5.3: the matrix of radon_1d,
+    leaf size b (the paper's c = 4), rank r = 10, |Omega| = c_obs n log2 n
+    observed entries (30 n log2 n at n = 1024 in the paper's Fig. 8), drawn
+    uniformly without replacement; the last floor(0.1 |Omega|) draws are the
+    test set."""
+    L = int(round(math.log2(n // b)))
+    if n != b << L:
+        raise ValueError("n must equal b * 2^L")
+    n_obs = int(round(c_obs * n * math.log2(n)))
+    seed = RADON_SEED_BASE + 16 * int(round(math.log2(n)))
+    i, j = draw_pairs(n, n_obs, seed + SEED_OMEGA)
+    vals = radon_1d(n, i, j)
+    n_test = int(math.floor(0.1 * n_obs))
+    n_train = n_obs - n_test
+    return Problem(name=f"radon_n{n}", n=n, L=L, b=b, r=r, omega=0.0, h=0.0, lam=lam, sweeps=sweeps,
+                   seed=seed, i=i[:n_train].copy(), j=j[:n_train].copy(), t=vals[:n_train].copy(),
+                   it=i[n_train:].copy(), jt=j[n_train:].copy(), tt=vals[n_train:].copy(),
+                   t_clean=vals[:n_train].copy())
+
+
+def lr2bf_gaussians(n: int, L: int, b: int, r: int, p: int, seed: int) -> np.ndarray:
+    """The Gaussian sketch matrices of the randomized low-rank to butterfly
+    conversion, CN(0, 1) from SplitMix64(seed), packed in the order the
+    conversion reads them: O_0 (n rows), then the left levels l = 1 .. H
+    (H = floor(L / 2)) and the right levels l = 1 .. L - H, b 2^{L-l} rows
+    each; r + p columns, row-major."""
+    H = L // 2
+    rows = n + sum(b << (L - l) for l in range(1, H + 1)) + sum(b << (L - l) for l in range(1, L - H + 1))
+    return SplitMix64(seed).cnormal(rows * (r + p))
 
 
 def batch_problems(count: int = 64, seed_base: int = BATCH_SEED_BASE,

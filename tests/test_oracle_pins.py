@@ -383,6 +383,80 @@ def test_lbfgs_monotone_and_reaches_stationarity():
     assert np.linalg.norm(g) < 1e-3 * np.linalg.norm(g0)
 
 
+def test_threaded_oracle_is_bit_identical_to_serial():
+    """The threaded variant runs independent systems and entries on several
+    threads with every sum in its serial order: sweeps, evaluations and
+    errors must be identical bit for bit to the serial oracle."""
+    p = synth.config(2, n_override=512)
+    X0 = synth.random_factors(p.n, p.L, p.r, 17, sigma=0.4)
+    out = {}
+    for nt in (1, 4):
+        with oracle.threads(nt):
+            X1, st = oracle.als_sweep(p.n, p.L, p.b, p.r, p.lam, X0, p.i, p.j, p.t)
+            X2, st2 = oracle.als_sweep(p.n, p.L, p.b, p.r, p.lam, X1, p.i, p.j, p.t)
+            x = oracle.eval_entries(p.n, p.L, p.b, p.r, X2, p.it, p.jt)
+            te = oracle.rel_err(p.n, p.L, p.b, p.r, X2, p.it, p.jt, p.tt)
+            out[nt] = (X2, st2, x, te)
+    (a, sa, xa, ta), (b_, sb, xb, tb) = out[1], out[4]
+    assert np.array_equal(a.view(np.float64), b_.view(np.float64))
+    assert np.array_equal(xa.view(np.float64), xb.view(np.float64))
+    assert sa == sb and ta == tb
+
+
+def _bfgs_matrix_direction(pairs, g):
+    """-H g with H the explicit BFGS inverse-Hessian recursion over the stored
+    pairs, oldest to newest: H <- (I - rho s y^T)^T-form update
+    H <- V^T H V + rho s s^T with V = I - rho y s^T, from H = gamma I with
+    gamma = s^T y / y^T y of the newest pair (Nocedal and Wright, eq. 7.19
+    and 7.20); gamma = 1 and H = I without pairs."""
+    dim = g.size
+    if not pairs:
+        return -g
+    s_new, y_new = pairs[-1]
+    H = (float(s_new @ y_new) / float(y_new @ y_new)) * np.eye(dim)
+    for s_, y_ in pairs:
+        rho = 1.0 / float(y_ @ s_)
+        V = np.eye(dim) - rho * np.outer(y_, s_)
+        H = V.T @ H @ V + rho * np.outer(s_, s_)
+    return -H @ g
+
+
+@pytest.mark.parametrize("n,L,b,r,memory", [(2, 1, 1, 1, 10), (2, 1, 1, 1, 3), (3, 0, 3, 1, 10),
+                                            (3, 0, 3, 1, 2)])
+def test_lbfgs_direction_is_the_explicit_bfgs_matrix_product(n, L, b, r, memory):
+    """The two-loop recursion of oracle.lbfgs must give exactly the direction
+    -H_k g_k of the explicit inverse-Hessian recursion over the last `memory`
+    accepted pairs (both with full memory and truncated memory).  A wrong
+    gamma pair, a swapped loop order or a dropped rho fails this check; the
+    step lengths must satisfy the Armijo rule from the stated first trial."""
+    lam = 1e-2
+    X0 = synth.random_factors(n, L, r, 5 + n + memory, sigma=0.7)
+    i, j = synth.random_pairs_full(n)
+    t = synth.helmholtz_line(n, 7.0, 1.0, i, j)
+    trace = []
+    iters = 12
+    oracle.lbfgs(n, L, b, r, lam, X0, i, j, t, iters, memory=memory, trace=trace)
+    assert len(trace) == iters
+    pairs = []
+    for k, (x, g, d, step, f) in enumerate(trace):
+        want = _bfgs_matrix_direction(pairs[-memory:], g)
+        if not float(g @ want) < 0.0:
+            want = -g
+        np.testing.assert_allclose(d, want, rtol=1e-9, atol=1e-12 * np.abs(want).max())
+        if k + 1 < len(trace):
+            x1, g1, _, _, f1 = trace[k + 1]
+            assert np.allclose(x1, x + step * d, rtol=0, atol=1e-14 * max(1.0, np.abs(x).max()))
+            assert f1 <= f + 1e-4 * step * float(g @ d)          # Armijo, c1 = 1e-4
+            s_, y_ = x1 - x, g1 - g
+            if float(s_ @ y_) > 1e-12 * np.linalg.norm(s_) * np.linalg.norm(y_):
+                pairs.append((s_, y_))
+        if k == 0:
+            first = 1.0 / np.linalg.norm(g)
+            # the first trial step is 1 / ||g||, halved until Armijo holds
+            assert any(abs(step - first * 0.5 ** h) <= 1e-15 * first for h in range(31))
+    assert len(pairs) > memory or memory >= iters
+
+
 # ----------------------------------------------------------- MLP oracle
 
 def test_bf16_rounding_is_nearest_even():
