@@ -88,7 +88,11 @@ typedef struct {
     int32_t init_kind;      /* bfc_complete: 0 = current factors,
                                1 = low-rank completion (Alg. 1 with L = 0,
                                    rank lr_rank, lr_sweeps sweeps) embedded
-                                   exactly into the butterfly              */
+                                   exactly into the butterfly,
+                               2 = the same completion converted by the
+                                   randomized Alg. 2 (bfc_lowrank_to_butterfly)
+                                   with CN(0, 1) Gaussians from SplitMix64
+                                   (seed + 1)                              */
     int32_t lr_rank;        /* rank R of the low-rank start (<= r)           */
     int32_t lr_sweeps;      /* sweeps of low-rank completion                 */
     int32_t values_on_device; /* 1: data pointers are device pointers        */
@@ -104,6 +108,8 @@ typedef struct {
                                three-term TF32 products, Kahan-folded every
                                32 entries) for r <= 8 and CUDA cores for
                                r > 8; 1 = CUDA cores (complex64 FMA) always */
+    int32_t lr2bf_oversample; /* oversampling p of Alg. 2 for init_kind 2
+                               (0 selects 5); r + p <= 32                   */
 } bfc_params;
 
 typedef struct {
@@ -201,6 +207,46 @@ bfc_status bfc_grad(bfc_ctx* ctx, int32_t include_reg, double* grad_packed,
 bfc_status bfc_lbfgs(bfc_ctx* ctx, int32_t iters, int32_t memory, bfc_sweep_stats* history,
                      int32_t history_cap, int32_t* done);
 
+/* ADAM completion (Alg. 4 with the update of Alg. 3, Sec. 4.1.2): `iters`
+ * outer iterations t = 1 .. iters.  Each updates S^1, S^2 .. S^{L+1},
+ * S^{L+2} in turn, every factor with the gradient of f (Eqs.
+ * (grad_butterfly_1/_l/_last), the regularization term lambda s included)
+ * taken at the newest values of all other factors, then
+ *   m <- beta1 m + (1 - beta1) g,  v <- beta2 v + (1 - beta2) g^2,
+ *   s <- s - alpha (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + sigma)
+ * on the real and the imaginary part of every complex parameter separately
+ * (FP64 moments and master factors; the residuals and gradient sums follow
+ * the context precision).  The moments start at zero on every call.  Stops
+ * after the iteration whose training error (Eq. (BF_convergence)) is below
+ * params.tol.  history (may be NULL) receives up to history_cap iteration
+ * records, *done (may be NULL) the iterations run.  EINVAL for iters < 0,
+ * alpha <= 0, beta1 or beta2 outside [0, 1), or sigma < 0. */
+bfc_status bfc_adam(bfc_ctx* ctx, int32_t iters, double alpha, double beta1, double beta2, double sigma,
+                    bfc_sweep_stats* history, int32_t history_cap, int32_t* done);
+
+/* ADF completion (Alg. 5, Sec. 4.1.3, with the orthogonalization sweeps of
+ * App. A.3): every iteration first makes every factor but S^1
+ * right-orthonormal (the right-to-left sweep: LQ of the slice pairs that
+ * differ in their lowest column bit, QR of the leaf blocks of S^{L+2}), forms
+ * the residual G = t - x, then for S^1, S^2 .. S^{L+1}, S^{L+2} in turn moves
+ * every fiber / slice s along N_s = sum_{e in s} G_e conj(a_e) - lambda s by
+ * the exact minimizer of f on that line,
+ *   alpha_s = ||N_s||^2 / (sum_{e in s} |a_e . N_s|^2 + lambda ||N_s||^2),
+ * updates G, and (except for S^{L+2}) QR-factors the factor's bond groups
+ * (R with a real positive diagonal) and multiplies R into the next factor.
+ * Stopping, history and done as bfc_adam.  EINVAL when b < r (the leaf
+ * blocks must have full column rank) or iters < 0. */
+bfc_status bfc_adf(bfc_ctx* ctx, int32_t iters, bfc_sweep_stats* history, int32_t history_cap, int32_t* done);
+
+/* Butterfly matrix-vector product (Eq. (butterfly-mat-vec), Sec. 3.2):
+ * U = X(S) V for nvec vectors in O((n r + L 2^{L+1} r^2) nvec) work, by the
+ * level-by-level contraction of the factors: the leaf sums of S^{L+2} with
+ * the vectors, then S^{L+1} .. S^2 each summing out one column bit, then
+ * S^1.  V and U are n x nvec row-major complex128 (V[j * nvec + q]), host or
+ * device arrays per params.values_on_device; arithmetic in the context
+ * precision.  EINVAL unless 1 <= nvec <= 4096. */
+bfc_status bfc_matvec(bfc_ctx* ctx, int32_t nvec, const double* V, double* U);
+
 /* Low-rank start (Sec. 4.2): low-rank matrix completion of rank R <= r from
  * the caller's starting factors A0, B0 (n x R packed complex128, X = A B^T),
  * `sweeps` sweeps of Alg. 1 with L = 0 on the GPU, then the exact embedding
@@ -208,6 +254,28 @@ bfc_status bfc_lbfgs(bfc_ctx* ctx, int32_t iters, int32_t memory, bfc_sweep_stat
  * Sets the context's factors.  A0/B0 follow values_on_device. */
 bfc_status bfc_lowrank_init(bfc_ctx* ctx, int32_t R, int32_t sweeps,
                             const double* A0, const double* B0);
+
+/* Randomized low-rank to butterfly conversion (Alg. 2, Sec. 4.2): sets the
+ * factors to a butterfly of X = A B^T (A, B: n x R complex128, 1 <= R <= r;
+ * host or device per params.values_on_device), in FP64.
+ *  1. M = A (B^T O_0), N = B (A^T O_0); for every leaf block, QR with column
+ *     pivoting of its b rows of M (of N) gives the block's rows of S^1
+ *     (S^{L+2}): the first r columns of Q; V = Q^H A(block) (W = Q^H B(block))
+ *     are its coefficients.
+ *  2. For the left levels l = 1 .. H = floor(L / 2): per column block nu the
+ *     sketch B(nu)^T O_l; the two slices of S^{l+1} that differ in i_{L-l}
+ *     are the halves of Q of the QRCP of [V_0; V_1] B(nu)^T O_l (their two
+ *     coefficient blocks stacked), and V := Q^H [V_0; V_1].  The right levels
+ *     l = 1 .. L - H fill S^{L+2-l} in the mirror order (pairs differing in
+ *     j_{L-l}, sketch A(tau)^T O'_l, halves of Q transposed).
+ *  3. The slices of S^{H+1} (z1 when H = 0) are right-multiplied by V W^T.
+ * `gaussians` holds the CN(0, 1) sketch matrices, r + p columns each,
+ * row-major, packed O_0 (n rows), O_1 .. O_H and O'_1 .. O'_{L-H}
+ * (b 2^{L-l} rows each); same memory kind as A and B.  With R <= r and leaf
+ * blocks of full column rank the butterfly reproduces A B^T to rounding.
+ * EINVAL unless 1 <= R <= r, p >= 0, r + p <= 32 and (L > 0) b >= R. */
+bfc_status bfc_lowrank_to_butterfly(bfc_ctx* ctx, int32_t R, const double* A, const double* B, int32_t p,
+                                    const double* gaussians);
 
 /* Full workflow (Sec. 4.3): optional low-rank start (init_kind 1, with a
  * CN(0, sigma^2) SplitMix64 start from params.seed), then ALS sweeps until

@@ -95,6 +95,9 @@ def _load():
         lib.bfo_als_sweep.argtypes = [i64, i32, i32, i32, dbl, vp, i64, vp, vp, vp,
                                       ctypes.POINTER(_Stats)]
         lib.bfo_als_sweep.restype = i64
+        lib.bfo_als_sweep_ridge.argtypes = [i64, i32, i32, i32, dbl, dbl, vp, i64, vp, vp, vp,
+                                            ctypes.POINTER(_Stats)]
+        lib.bfo_als_sweep_ridge.restype = i64
         lib.bfo_grad.argtypes = [i64, i32, i32, i32, dbl, i32, vp, i64, vp, vp, vp, vp, vp]
         lib.bfo_grad.restype = None
         lib.bfo_embed_lowrank.argtypes = [i64, i32, i32, i32, i32, vp, vp, vp, vp]
@@ -187,14 +190,16 @@ def objective(n, L, b, r, lam, packed, i, j, t) -> float:
                                        _ptr(j), _ptr(t)))
 
 
-def als_sweep(n, L, b, r, lam, packed, i, j, t):
-    """One ALS sweep (Alg. 1).  Returns (new_packed, stats dict)."""
+def als_sweep(n, L, b, r, lam, packed, i, j, t, ridge_rel=0.0):
+    """One ALS sweep (Alg. 1).  Returns (new_packed, stats dict).  ridge_rel
+    > 0 solves every system with max(lam, ridge_rel * trace(Gram) / dim),
+    the regularization the precision form uses."""
     out = _c128(packed).copy()
     t = _c128(t)
     i, j = _i32(i), _i32(j)
     st = _Stats()
-    _load().bfo_als_sweep(n, L, b, r, lam, _ptr(out), len(i), _ptr(i), _ptr(j), _ptr(t),
-                          ctypes.byref(st))
+    _load().bfo_als_sweep_ridge(n, L, b, r, lam, float(ridge_rel), _ptr(out), len(i), _ptr(i), _ptr(j),
+                                _ptr(t), ctypes.byref(st))
     return out, {"train_rel_err": st.train_rel_err, "objective": st.objective,
                  "singular": int(st.singular)}
 

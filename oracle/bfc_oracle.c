@@ -284,7 +284,7 @@ static int chol_solve(cplx* K, const cplx* y, cplx* s, int d, double piv_tol)
  * (Alg. 1, normal-equation lines, complex form) and overwrite `target` with
  * K^{-1} y.  Returns 1 (target untouched) if K is numerically singular. */
 static int block_solve(const cplx* A, const cplx* tv, int64_t cnt, int d,
-                       double lambda, cplx* target)
+                       double lambda, double ridge_rel, cplx* target)
 {
     cplx* K = (cplx*)calloc((size_t)d * d, sizeof(cplx));
     cplx y[BFO_MAX_R * BFO_MAX_R], s[BFO_MAX_R * BFO_MAX_R];
@@ -297,6 +297,12 @@ static int block_solve(const cplx* A, const cplx* tv, int64_t cnt, int d,
             for (int q = 0; q <= p; ++q) K[p * d + q] += ca * a[q];
         }
     }
+    /* ridge floor (the precision form's reading of the regularization):
+     * lambda is raised to ridge_rel * trace(Gram) / d when that is larger;
+     * ridge_rel = 0 leaves lambda as it is */
+    double gram_trace = 0.0;
+    for (int p = 0; p < d; ++p) gram_trace += creal(K[p * d + p]);
+    if (ridge_rel > 0.0 && ridge_rel * gram_trace / d > lambda) lambda = ridge_rel * gram_trace / d;
     double trace = 0.0;
     for (int p = 0; p < d; ++p) {
         K[p * d + p] += lambda;
@@ -320,7 +326,7 @@ static int block_solve(const cplx* A, const cplx* tv, int64_t cnt, int d,
  * number of singular blocks. */
 static int64_t solve_blocks(const bfo_factors* F, int level, const int64_t* order, const int64_t* start,
                             int64_t K, const cplx* env_a, const cplx* env_b, const cplx* tv_all,
-                            double lambda, cplx* target)
+                            double lambda, double ridge_rel, cplx* target)
 {
     const int r = F->r;
     const int mid = level >= 1 && level <= F->L;
@@ -348,7 +354,7 @@ static int64_t solve_blocks(const bfo_factors* F, int level, const int64_t* orde
                 }
                 tv[q] = tv_all[e];
             }
-            singular += block_solve(A, tv, cnt, d, lambda, target + k * d);
+            singular += block_solve(A, tv, cnt, d, lambda, ridge_rel, target + k * d);
         }
         free(A);
         free(tv);
@@ -377,9 +383,9 @@ typedef struct {
  * 4. S^{L+2}: for each column j, solve with a_e = h_{L+1}(e).
  * 5. Statistics on the training set with the new factors.
  * Returns the number of singular (skipped) systems. */
-int64_t bfo_als_sweep(int64_t n, int L, int b, int r, double lambda,
-                      double* packed, int64_t N, const int32_t* ii,
-                      const int32_t* jj, const double* t, bfo_stats* st)
+int64_t bfo_als_sweep_ridge(int64_t n, int L, int b, int r, double lambda, double ridge_rel,
+                            double* packed, int64_t N, const int32_t* ii,
+                            const int32_t* jj, const double* t, bfo_stats* st)
 {
     bfo_factors F = view(n, L, b, r, packed);
     const int64_t S = F.S;
@@ -415,7 +421,7 @@ int64_t bfo_als_sweep(int64_t n, int L, int b, int r, double lambda,
     /* 2. S^1 fibers, grouped by row i */
     for (int64_t e = 0; e < N; ++e) key[e] = ii[e];
     group_by_key(key, N, n, order, start);
-    singular += solve_blocks(&F, 0, order, start, n, w, NULL, tv_all, lambda, F.z1);
+    singular += solve_blocks(&F, 0, order, start, n, w, NULL, tv_all, lambda, ridge_rel, F.z1);
     for (int64_t e = 0; e < N; ++e)
         memcpy(h + e * r, F.z1 + (int64_t)ii[e] * r, (size_t)r * sizeof(cplx));
 
@@ -423,7 +429,7 @@ int64_t bfo_als_sweep(int64_t n, int L, int b, int r, double lambda,
     for (int m = 1; m <= L; ++m) {
         for (int64_t e = 0; e < N; ++e) key[e] = bfo_slice_id(ii[e], jj[e], m, L, b);
         group_by_key(key, N, S, order, start);
-        singular += solve_blocks(&F, m, order, start, S, h, w + (int64_t)m * N * r, tv_all, lambda,
+        singular += solve_blocks(&F, m, order, start, S, h, w + (int64_t)m * N * r, tv_all, lambda, ridge_rel,
                                  slice_ptr(&F, m, 0));
 #pragma omp parallel for schedule(static) num_threads(g_threads)
         for (int64_t e = 0; e < N; ++e) {
@@ -441,7 +447,7 @@ int64_t bfo_als_sweep(int64_t n, int L, int b, int r, double lambda,
     /* 4. S^{L+2} fibers, grouped by column j, design h_{L+1} */
     for (int64_t e = 0; e < N; ++e) key[e] = jj[e];
     group_by_key(key, N, n, order, start);
-    singular += solve_blocks(&F, L + 1, order, start, n, h, NULL, tv_all, lambda, F.zL);
+    singular += solve_blocks(&F, L + 1, order, start, n, h, NULL, tv_all, lambda, ridge_rel, F.zL);
 
     free(w); free(h); free(hn); free(key); free(order); free(start);
     (void)d2;
@@ -452,6 +458,14 @@ int64_t bfo_als_sweep(int64_t n, int L, int b, int r, double lambda,
         st->singular = singular;
     }
     return singular;
+}
+
+/* One ALS sweep with the plain regularization lambda (Alg. 1). */
+int64_t bfo_als_sweep(int64_t n, int L, int b, int r, double lambda,
+                      double* packed, int64_t N, const int32_t* ii,
+                      const int32_t* jj, const double* t, bfo_stats* st)
+{
+    return bfo_als_sweep_ridge(n, L, b, r, lambda, 0.0, packed, N, ii, jj, t, st);
 }
 
 /* -------------------------------------------------------------- gradient */

@@ -30,6 +30,7 @@ __all__ = [
     "bfc_mlp_create", "bfc_mlp_dims", "bfc_mlp_num_params", "bfc_mlp_get_params", "bfc_mlp_set_params",
     "bfc_mlp_set_scaling", "bfc_mlp_forward", "bfc_mlp_grad", "bfc_mlp_train", "bfc_mlp_destroy",
     "bfc_init_learned", "bfc_canonicalize", "Mlp", "bfc_measure_alu_peaks", "bfc_inject_fault",
+    "bfc_adam", "bfc_adf", "bfc_matvec", "bfc_lowrank_to_butterfly",
 ]
 
 PREC_FP64 = 0
@@ -47,6 +48,7 @@ exported_symbols = (
     "bfc_mlp_create", "bfc_mlp_dims", "bfc_mlp_num_params", "bfc_mlp_get_params", "bfc_mlp_set_params",
     "bfc_mlp_set_scaling", "bfc_mlp_forward", "bfc_mlp_grad", "bfc_mlp_train", "bfc_mlp_destroy",
     "bfc_init_learned", "bfc_canonicalize", "bfc_measure_alu_peaks", "bfc_inject_fault",
+    "bfc_adam", "bfc_adf", "bfc_matvec", "bfc_lowrank_to_butterfly",
     "bfc_profile_enable", "bfc_profile_read", "bfc_last_error", "bfc_destroy",
 )
 
@@ -64,7 +66,7 @@ class Params(ctypes.Structure):
                 ("init_kind", ctypes.c_int32), ("lr_rank", ctypes.c_int32),
                 ("lr_sweeps", ctypes.c_int32), ("values_on_device", ctypes.c_int32),
                 ("refine_sweeps", ctypes.c_int32), ("ridge_rel", ctypes.c_double),
-                ("gram_impl", ctypes.c_int32)]
+                ("gram_impl", ctypes.c_int32), ("lr2bf_oversample", ctypes.c_int32)]
 
 
 class SweepStats(ctypes.Structure):
@@ -163,6 +165,14 @@ def load():
         lib.bfc_get_order.restype = i32
         lib.bfc_residual_noalloc.argtypes = [i64, i32, i32, i32, vp, i64, vp, vp, vp, vp, vp]
         lib.bfc_residual_noalloc.restype = i32
+        lib.bfc_adam.argtypes = [vp, i32, dbl, dbl, dbl, dbl, sp, i32, ctypes.POINTER(i32)]
+        lib.bfc_adam.restype = i32
+        lib.bfc_adf.argtypes = [vp, i32, sp, i32, ctypes.POINTER(i32)]
+        lib.bfc_adf.restype = i32
+        lib.bfc_matvec.argtypes = [vp, i32, vp, vp]
+        lib.bfc_matvec.restype = i32
+        lib.bfc_lowrank_to_butterfly.argtypes = [vp, i32, vp, vp, i32, vp]
+        lib.bfc_lowrank_to_butterfly.restype = i32
         lib.bfc_inject_fault.argtypes = [vp, i32]
         lib.bfc_inject_fault.restype = i32
         lib.bfc_profile_enable.argtypes = [vp, i32]
@@ -257,6 +267,29 @@ def bfc_lbfgs(ctx, iters: int, memory: int = 10):
     done = ctypes.c_int32(0)
     _check(load().bfc_lbfgs(ctx, iters, memory, hist, iters, ctypes.byref(done)), ctx)
     return [hist[q] for q in range(done.value)]
+
+
+def bfc_adam(ctx, iters: int, alpha: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+             sigma: float = 1e-8):
+    hist = (SweepStats * max(iters, 1))()
+    done = ctypes.c_int32(0)
+    _check(load().bfc_adam(ctx, iters, alpha, beta1, beta2, sigma, hist, iters, ctypes.byref(done)), ctx)
+    return [hist[q] for q in range(done.value)]
+
+
+def bfc_adf(ctx, iters: int):
+    hist = (SweepStats * max(iters, 1))()
+    done = ctypes.c_int32(0)
+    _check(load().bfc_adf(ctx, iters, hist, iters, ctypes.byref(done)), ctx)
+    return [hist[q] for q in range(done.value)]
+
+
+def bfc_matvec(ctx, nvec: int, V, U):
+    _check(load().bfc_matvec(ctx, nvec, _ptr(V), _ptr(U)), ctx)
+
+
+def bfc_lowrank_to_butterfly(ctx, R: int, A, B, p: int, gaussians):
+    _check(load().bfc_lowrank_to_butterfly(ctx, R, _ptr(A), _ptr(B), p, _ptr(gaussians)), ctx)
 
 
 def bfc_lowrank_init(ctx, R: int, sweeps: int, A0, B0):
@@ -470,12 +503,12 @@ class Completion:
 
     def __init__(self, n, L, b, r, lam, i, j, t, it=None, jt=None, tt=None, prec=PREC_FP64,
                  max_sweeps=20, tol=1e-3, seed=0, init_kind=0, lr_rank=0, lr_sweeps=10,
-                 refine_sweeps=0, ridge_rel=0.0, gram_impl=GRAM_TENSOR):
+                 refine_sweeps=0, ridge_rel=0.0, gram_impl=GRAM_TENSOR, lr2bf_oversample=0):
         self.n, self.L, self.b, self.r = int(n), int(L), int(b), int(r)
         self.params = Params(n=n, L=L, b=b, r=r, lam=lam, prec=prec, max_sweeps=max_sweeps, tol=tol,
                              seed=seed, init_kind=init_kind, lr_rank=lr_rank, lr_sweeps=lr_sweeps,
                              values_on_device=0, refine_sweeps=refine_sweeps, ridge_rel=ridge_rel,
-                             gram_impl=gram_impl)
+                             gram_impl=gram_impl, lr2bf_oversample=lr2bf_oversample)
         self.P = bfc_num_params(n, L, b, r)
         self._nnz = len(i)
         self.ctx = bfc_create(self.params, i, j, t, it, jt, tt)
@@ -505,9 +538,28 @@ class Completion:
     def lbfgs(self, iters, memory=10):
         return [h.as_dict() for h in bfc_lbfgs(self.ctx, iters, memory)]
 
+    def adam(self, iters, alpha=1e-3, beta1=0.9, beta2=0.999, sigma=1e-8):
+        return [h.as_dict() for h in bfc_adam(self.ctx, iters, alpha, beta1, beta2, sigma)]
+
+    def adf(self, iters):
+        return [h.as_dict() for h in bfc_adf(self.ctx, iters)]
+
+    def matvec(self, V):
+        """X(S) V for V of shape (n,) or (n, nvec), complex128."""
+        V = _host_c128(V)
+        one = V.ndim == 1
+        Vm = np.ascontiguousarray(V.reshape(self.n, -1))
+        U = np.zeros_like(Vm)
+        bfc_matvec(self.ctx, Vm.shape[1], Vm, U)
+        return U.ravel() if one else U
+
     def lowrank_init(self, A0, B0, sweeps):
         A0, B0 = _host_c128(A0), _host_c128(B0)
         bfc_lowrank_init(self.ctx, A0.shape[1], sweeps, A0, B0)
+
+    def lowrank_to_butterfly(self, A, B, p, gaussians):
+        A, B, G = _host_c128(A), _host_c128(B), _host_c128(gaussians)
+        bfc_lowrank_to_butterfly(self.ctx, A.shape[1], A, B, p, G)
 
     def order(self, level):
         N = int(self._nnz)

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "bfc_fo.h"
 #include "bfc_internal.h"
 #include "bfc_ops.h"
 #include "bfc_util.h"
@@ -317,7 +318,8 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
     if (p.gram_impl != 0 && p.gram_impl != 1) return fail(nullptr, BFC_EINVAL, "gram_impl must be 0 or 1");
     if (p.max_sweeps < 0 || p.refine_sweeps < 0 || p.lr_sweeps < 0 || p.lr_rank < 0)
         return fail(nullptr, BFC_EINVAL, "sweep counts and lr_rank must be >= 0");
-    if (p.init_kind != 0 && p.init_kind != 1) return fail(nullptr, BFC_EINVAL, "init_kind must be 0 or 1");
+    if (p.init_kind < 0 || p.init_kind > 2) return fail(nullptr, BFC_EINVAL, "init_kind must be 0, 1 or 2");
+    if (p.lr2bf_oversample < 0) return fail(nullptr, BFC_EINVAL, "lr2bf_oversample must be >= 0");
     if (in.nnz <= 0 || in.nnz >= ((int64_t)1 << 31) - 1) return fail(nullptr, BFC_EINVAL, "nnz must be in [1, 2^31-2]");
     if (in.ntest < 0 || in.ntest >= ((int64_t)1 << 31) - 1) return fail(nullptr, BFC_EINVAL, "bad ntest");
     if (!in.i || !in.j || !in.t) return fail(nullptr, BFC_EINVAL, "null training data");
@@ -785,10 +787,29 @@ bfc_status bfc_lbfgs(bfc_ctx* ctx, int32_t iters, int32_t memory, bfc_sweep_stat
     return lbfgs_impl(c, iters, memory, history, history_cap, done);
 }
 
-bfc_status bfc_lowrank_init(bfc_ctx* ctx, int32_t R, int32_t sweeps, const double* A0, const double* B0)
+// Alg. 2 on device A, B (n x R) with host or device Gaussians (gkind) into
+// the context's FP64 factors; the compute copies are refreshed.
+static bfc_status lr2bf_into(Ctx* c, int R, const double2* A, const double2* B, const double* gauss,
+                             cudaMemcpyKind gkind, int p)
 {
-    Ctx* c = (Ctx*)ctx;
-    if (!c) return BFC_EINVAL;
+    const int64_t gcount = lr2bf_gaussian_count(c->n, c->L, c->b, c->r, p);
+    const size_t gb = ((size_t)gcount * 16 + 255) / 256 * 256;
+    const size_t sb = lr2bf_scratch_bytes(c->n, c->L, c->b, R, c->r, p);
+    BFC_TRY(ensure_tmp(c, gb + sb));
+    double2* G = (double2*)c->d_tmp;
+    BFC_CK(c, cudaMemcpyAsync(G, gauss, (size_t)gcount * 16, gkind, c->stream));
+    cudaError_t e = lr2bf_run(A, B, G, c->n, c->L, c->b, R, c->r, p, c->z1d, c->Zd, c->zLd, (char*)c->d_tmp + gb,
+                              c->stream);
+    if (e != cudaSuccess) return fail(c, BFC_ECUDA, std::string("low-rank to butterfly: ") + cudaGetErrorString(e));
+    BFC_TRY(refresh_copies(c));
+    return sync(c);
+}
+
+// Low-rank start: rank-R completion (Alg. 1 with L = 0) from A0, B0, then the
+// exact embedding (gauss == nullptr) or Alg. 2 with the given host Gaussians.
+static bfc_status lowrank_init_impl(Ctx* c, int32_t R, int32_t sweeps, const double* A0, const double* B0,
+                                    const double* gauss, int p)
+{
     if (R < 1 || R > c->r || sweeps < 0 || !A0 || !B0) return fail(c, BFC_EINVAL, "bad low-rank arguments");
     // Low-rank completion is Alg. 1 with L = 0 and leaf size n on the same data.
     bfc_params lp = c->P;
@@ -816,6 +837,12 @@ bfc_status bfc_lowrank_init(bfc_ctx* ctx, int32_t R, int32_t sweeps, const doubl
         bfc_destroy(lr);
         return fail(c, st, "low-rank completion: " + m);
     }
+    if (gauss) {
+        // Alg. 2 reads lc's factors on c->stream (lr2bf_into synchronizes)
+        st = lr2bf_into(c, R, lc->z1d, lc->zLd, gauss, cudaMemcpyHostToDevice, p);
+        bfc_destroy(lr);
+        return st;
+    }
     launch_embed(lc->z1d, lc->zLd, c->n, R, c->r, (int64_t)c->L * c->S, c->z1d, c->Zd, c->zLd, c->stream);
     cudaError_t e = cudaGetLastError();
     // the embedding reads lc's buffers on c->stream: finish before freeing lc
@@ -824,6 +851,37 @@ bfc_status bfc_lowrank_init(bfc_ctx* ctx, int32_t R, int32_t sweeps, const doubl
     if (e != cudaSuccess) return fail(c, BFC_ECUDA, std::string("embed: ") + cudaGetErrorString(e));
     BFC_TRY(refresh_copies(c));
     return sync(c);
+}
+
+bfc_status bfc_lowrank_init(bfc_ctx* ctx, int32_t R, int32_t sweeps, const double* A0, const double* B0)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    return lowrank_init_impl(c, R, sweeps, A0, B0, nullptr, 0);
+}
+
+bfc_status bfc_lowrank_to_butterfly(bfc_ctx* ctx, int32_t R, const double* A, const double* B, int32_t p,
+                                    const double* gaussians)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    if (R < 1 || R > c->r || p < 0 || c->r + p > 32 || !A || !B || !gaussians)
+        return fail(c, BFC_EINVAL, "low-rank to butterfly needs 1 <= R <= r, p >= 0, r + p <= 32 and all arrays");
+    if (c->L > 0 && c->b < R)
+        return fail(c, BFC_EINVAL, "low-rank to butterfly: leaf size b must be >= R");
+    if (c->P.values_on_device)
+        return lr2bf_into(c, R, (const double2*)A, (const double2*)B, gaussians, cudaMemcpyDeviceToDevice, p);
+    // host A, B: staged in a device buffer of the context's own
+    double2* AB = nullptr;
+    const size_t half = (size_t)c->n * R * 16;
+    BFC_TRY(dalloc(c, (void**)&AB, 2 * half, "low-rank factors"));
+    BFC_CK(c, cudaMemcpyAsync(AB, A, half, cudaMemcpyHostToDevice, c->stream));
+    BFC_CK(c, cudaMemcpyAsync((char*)AB + half, B, half, cudaMemcpyHostToDevice, c->stream));
+    const bfc_status st = lr2bf_into(c, R, AB, (const double2*)((char*)AB + half), gaussians,
+                                     cudaMemcpyHostToDevice, p);
+    cudaStreamSynchronize(c->stream);
+    dfree(c, AB);
+    return st;
 }
 
 // SplitMix64 (Steele, Lea, Flood 2014) + Box-Muller CN(0, sigma^2) start, the
@@ -854,8 +912,7 @@ static void splitmix_cnormal(uint64_t seed, uint64_t& k, int64_t count, double s
 // Start of the full workflow: the optional low-rank start (init_kind 1).
 static bfc_status complete_init(Ctx* c)
 {
-    bfc_ctx* ctx = (bfc_ctx*)c;
-    if (c->P.init_kind == 1) {
+    if (c->P.init_kind == 1 || c->P.init_kind == 2) {
         const int R = c->P.lr_rank > 0 ? c->P.lr_rank : c->r;
         if (R > c->r) return fail(c, BFC_EINVAL, "lr_rank > r");
         // rms of the training values
@@ -869,9 +926,20 @@ static bfc_status complete_init(Ctx* c)
         std::vector<double> A, B;
         splitmix_cnormal(c->P.seed, k, c->n * R, sigma, A);
         splitmix_cnormal(c->P.seed, k, c->n * R, sigma, B);
+        // init_kind 2: Alg. 2's Gaussians from a second SplitMix64 stream,
+        // seed params.seed + 1, CN(0, 1), in the order the conversion reads them
+        std::vector<double> G;
+        const int p = c->P.lr2bf_oversample > 0 ? c->P.lr2bf_oversample : 5;
+        if (c->P.init_kind == 2) {
+            if (c->r + p > 32) return fail(c, BFC_EINVAL, "r + lr2bf_oversample must be <= 32");
+            if (c->L > 0 && c->b < R) return fail(c, BFC_EINVAL, "Alg. 2 needs b >= lr_rank");
+            uint64_t kg = 0;
+            splitmix_cnormal(c->P.seed + 1, kg, lr2bf_gaussian_count(c->n, c->L, c->b, c->r, p), 1.0, G);
+        }
         const int32_t saved = c->P.values_on_device;
         c->P.values_on_device = 0;
-        bfc_status st = bfc_lowrank_init(ctx, R, c->P.lr_sweeps, A.data(), B.data());
+        bfc_status st = lowrank_init_impl(c, R, c->P.lr_sweeps, A.data(), B.data(),
+                                          c->P.init_kind == 2 ? G.data() : nullptr, p);
         c->P.values_on_device = saved;
         BFC_TRY(st);
     }
@@ -956,6 +1024,114 @@ bfc_status bfc_complete(bfc_ctx* ctx, bfc_sweep_stats* history, int32_t history_
     bfc_status st = complete_refine(c, history, history_cap, &done);
     if (nsweeps) *nsweeps = done;
     return st;
+}
+
+}  // extern "C"
+
+// Statistics of one first-order iteration: the training residual partials
+// (per column fiber in d_red) are reduced, ||S||^2 and the test error added.
+static bfc_status fo_iter_stats(Ctx* c, bfc_sweep_stats* out, int64_t launched0)
+{
+    {
+        ProfScope ps(c, "reduce");
+        launch_reduce_pairs(c->d_red, c->n, c->d_scalars + 0, c->stream);
+    }
+    BFC_LAUNCH_CHECK(c, "reduce");
+    BFC_TRY(factor_sumsq(c, 2));
+    BFC_TRY(test_error(c, 3));
+    BFC_CK(c, cudaEventRecord(c->ev1, c->stream));
+    c->sweeps_done += 1;
+    BFC_TRY(sync(c));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    BFC_TRY(collect_stats(c, out, ms));
+    out->launches = c->n_launch - launched0;
+    out->gram_impl = -1;
+    return BFC_OK;
+}
+
+// Runs `iters` iterations of a first-order method (one_iter enqueues one),
+// recording statistics and stopping early once the training error is below
+// params.tol.
+template <typename F>
+static bfc_status fo_run(Ctx* c, int32_t iters, bfc_sweep_stats* history, int32_t cap, int32_t* done, F one_iter)
+{
+    if (done) *done = 0;
+    for (int32_t it = 1; it <= iters; ++it) {
+        const int64_t l0 = c->n_launch;
+        BFC_CK(c, cudaMemsetAsync(c->d_count, 0, 3 * sizeof(unsigned long long), c->stream));
+        BFC_CK(c, cudaEventRecord(c->ev0, c->stream));
+        BFC_TRY(one_iter(it));
+        bfc_sweep_stats st{};
+        BFC_TRY(fo_iter_stats(c, &st, l0));
+        st.sweep = it;
+        if (history && it <= cap) history[it - 1] = st;
+        if (done) *done = it;
+        if (st.train_rel_err < c->P.tol) break;
+    }
+    return BFC_OK;
+}
+
+extern "C" {
+
+bfc_status bfc_matvec(bfc_ctx* ctx, int32_t nvec, const double* V, double* U)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    if (nvec < 1 || nvec > 4096 || !V || !U) return fail(c, BFC_EINVAL, "matvec needs 1 <= nvec <= 4096 and vectors");
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t vb = up((size_t)c->n * nvec * 16);
+    const size_t yb = up((size_t)c->S * nvec * c->r * c->vsz);
+    BFC_TRY(ensure_tmp(c, 2 * vb + 2 * yb));
+    char* base = (char*)c->d_tmp;
+    double2* Vd = (double2*)base;
+    double2* Ud = (double2*)(base + vb);
+    void* y0 = base + 2 * vb;
+    void* y1 = base + 2 * vb + yb;
+    BFC_CK(c, cudaMemcpyAsync(Vd, V, (size_t)c->n * nvec * 16, in_kind(c), c->stream));
+    BFC_TRY(get_fo_ops(c->fp32, c->r)->matvec(c, nvec, Vd, Ud, y0, y1));
+    BFC_CK(c, cudaMemcpyAsync(U, Ud, (size_t)c->n * nvec * 16, out_kind(c), c->stream));
+    return sync(c);
+}
+
+bfc_status bfc_adam(bfc_ctx* ctx, int32_t iters, double alpha, double beta1, double beta2, double sigma,
+                    bfc_sweep_stats* history, int32_t history_cap, int32_t* done)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    if (done) *done = 0;
+    if (iters < 0 || !(alpha > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) ||
+        !(sigma >= 0.0))
+        return fail(c, BFC_EINVAL, "ADAM needs iters >= 0, alpha > 0, 0 <= beta1, beta2 < 1, sigma >= 0");
+    if (!c->adam_m) {
+        BFC_TRY(dalloc(c, (void**)&c->adam_m, (size_t)c->Pn * sizeof(double2), "ADAM first moments"));
+        BFC_TRY(dalloc(c, (void**)&c->adam_v, (size_t)c->Pn * sizeof(double2), "ADAM second moments"));
+    }
+    BFC_CK(c, cudaMemsetAsync(c->adam_m, 0, (size_t)c->Pn * sizeof(double2), c->stream));
+    BFC_CK(c, cudaMemsetAsync(c->adam_v, 0, (size_t)c->Pn * sizeof(double2), c->stream));
+    const FoOps* fo = get_fo_ops(c->fp32, c->r);
+    return fo_run(c, iters, history, history_cap, done, [&](int32_t it) {
+        AdamHyper hp;
+        hp.alpha = alpha;
+        hp.beta1 = beta1;
+        hp.beta2 = beta2;
+        hp.sigma = sigma;
+        hp.inv1 = 1.0 / (1.0 - pow(beta1, (double)it));
+        hp.inv2 = 1.0 / (1.0 - pow(beta2, (double)it));
+        return fo->adam_iter(c, hp, c->adam_m, c->adam_v);
+    });
+}
+
+bfc_status bfc_adf(bfc_ctx* ctx, int32_t iters, bfc_sweep_stats* history, int32_t history_cap, int32_t* done)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    if (done) *done = 0;
+    if (iters < 0) return fail(c, BFC_EINVAL, "iters must be >= 0");
+    if ((c->L > 0 && c->b < c->r) || c->n < c->r)
+        return fail(c, BFC_EINVAL, "ADF orthogonalizes b x r leaf blocks: needs b >= r");
+    const FoOps* fo = get_fo_ops(c->fp32, c->r);
+    return fo_run(c, iters, history, history_cap, done, [&](int32_t) { return fo->adf_iter(c); });
 }
 
 bfc_status bfc_canonicalize(bfc_ctx* ctx)

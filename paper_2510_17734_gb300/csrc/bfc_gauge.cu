@@ -173,6 +173,132 @@ __global__ void k_canon_level(double2* __restrict__ z1, double2* __restrict__ Z,
     }
 }
 
+// rows[q] := rows[q] X for `count` rows of r values (row vectors), X r x r
+template <int R>
+__device__ void right_mul_rows(double2* rows, int64_t count, const double2 (*X)[R], int lane)
+{
+    for (int64_t q = lane; q < count; q += 32) {
+        double2 v[R];
+#pragma unroll
+        for (int c = 0; c < R; ++c) v[c] = rows[(size_t)q * R + c];
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+            double sx = 0.0, sy = 0.0;
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const double2 x = X[k][c];
+                sx += v[k].x * x.x - v[k].y * x.y;
+                sy += v[k].x * x.y + v[k].y * x.x;
+            }
+            rows[(size_t)q * R + c] = d2(sx, sy);
+        }
+    }
+    __syncwarp();
+}
+
+// Right-to-left orthogonalization, one level (the mirror of k_canon_level):
+//  * level L + 1, leaf block p of columns j: M = zL[p b .. p b + b - 1]
+//    (b x r) = Q R, zL := Q and R^T right-multiplies the slices
+//    (i_0 << L) | p of S^{L+1} (for L = 0: every row z1[i]);
+//  * level m = L .. 1, group g: the two slices k = 2g, 2g + 1 of S^{m+1}
+//    (differing in j_{m-1}, bit 0) form [Z0 | Z1] = R^H Q^H, computed as the
+//    QR of the stacked conjugate transposes [Z0^H; Z1^H] (2r x r); Z_b :=
+//    (half b of Q)^H, and R^H right-multiplies the two slices of S^m that
+//    share the bond, ((g >> (m-1)) << m) | (c << (m-1)) | (g mod 2^(m-1)),
+//    or, for m = 1, the rows z1[i] of leaf block p_i = g.
+template <int R>
+__global__ void k_rl_level(double2* __restrict__ z1, double2* __restrict__ Z, double2* __restrict__ zL, int64_t n,
+                           int L, int b, int level, int ngroups)
+{
+    __shared__ double2 Rs[4][R][R];
+    __shared__ double2 Xs[4][R][R];
+    __shared__ double2 Ms[4][2 * R * R];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * 4 + w;
+    if (g >= ngroups) return;
+    const int64_t S = (int64_t)1 << (L + 1);
+    auto slice = [&](int m, int64_t k) { return Z + ((size_t)(m - 1) * S + k) * R * R; };   // Z[m][k], m = 1..L
+    GroupRows M;
+    M.r = R;
+    if (level == L + 1) {
+        M.a = zL + (size_t)g * b * R;
+        M.b = M.a;
+        M.split = b;
+        M.nrows = b;
+        warp_qr<R>(M, Rs[w], lane);
+        // X = R^T
+        for (int x = lane; x < R * R; x += 32) Xs[w][x / R][x % R] = Rs[w][x % R][x / R];
+        __syncwarp();
+        if (L == 0) {
+            right_mul_rows<R>(z1, n, Xs[w], lane);
+        } else {
+            for (int i0 = 0; i0 < 2; ++i0)
+                right_mul_rows<R>(slice(L, ((int64_t)i0 << L) | g), R, Xs[w], lane);
+        }
+        return;
+    }
+    const int m = level;
+    double2* Z0 = slice(m, 2 * (int64_t)g);
+    double2* Z1 = slice(m, 2 * (int64_t)g + 1);
+    // stacked conjugate transposes: row q < R is column q of Z0, conjugated
+    for (int x = lane; x < 2 * R * R; x += 32) {
+        const int q = x / R, a = x % R;
+        const double2 v = q < R ? Z0[a * R + q] : Z1[a * R + (q - R)];
+        Ms[w][x] = d2(v.x, -v.y);
+    }
+    __syncwarp();
+    M.a = Ms[w];
+    M.b = Ms[w];
+    M.split = 2 * R;
+    M.nrows = 2 * R;
+    warp_qr<R>(M, Rs[w], lane);
+    for (int x = lane; x < 2 * R * R; x += 32) {
+        const int q = x / R, a = x % R;       // Q[q][a]
+        const double2 v = Ms[w][x];
+        if (q < R) Z0[a * R + q] = d2(v.x, -v.y);
+        else Z1[a * R + (q - R)] = d2(v.x, -v.y);
+    }
+    // X = R^H
+    for (int x = lane; x < R * R; x += 32) {
+        const double2 v = Rs[w][x % R][x / R];
+        Xs[w][x / R][x % R] = d2(v.x, -v.y);
+    }
+    __syncwarp();
+    if (m > 1) {
+        for (int c = 0; c < 2; ++c) {
+            const int64_t kk = ((int64_t)(g >> (m - 1)) << m) | ((int64_t)c << (m - 1)) | (g & ((1 << (m - 1)) - 1));
+            right_mul_rows<R>(slice(m - 1, kk), R, Xs[w], lane);
+        }
+    } else {
+        right_mul_rows<R>(z1 + (size_t)g * b * R, b, Xs[w], lane);
+    }
+}
+
+template <int R>
+cudaError_t rl_all(double2* z1, double2* Z, double2* zL, int64_t n, int L, int b, cudaStream_t st)
+{
+    const int g0 = L == 0 ? 1 : (int)(n / b);
+    k_rl_level<R><<<(g0 + 3) / 4, 128, 0, st>>>(z1, Z, zL, n, L, L == 0 ? (int)n : b, L + 1, g0);
+    for (int m = L; m >= 1; --m) {
+        const int g = 1 << L;
+        k_rl_level<R><<<(g + 3) / 4, 128, 0, st>>>(z1, Z, zL, n, L, b, m, g);
+    }
+    return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t canon_one(double2* z1, double2* Z, double2* zL, int64_t n, int L, int b, int level, cudaStream_t st)
+{
+    if (level == 0) {
+        const int g0 = L == 0 ? 1 : (int)(n / b);
+        k_canon_level<R><<<(g0 + 3) / 4, 128, 0, st>>>(z1, Z, zL, n, L, L == 0 ? (int)n : b, 0, g0);
+    } else {
+        const int g = 1 << L;
+        k_canon_level<R><<<(g + 3) / 4, 128, 0, st>>>(z1, Z, zL, n, L, b, level, g);
+    }
+    return cudaGetLastError();
+}
+
 template <int R>
 cudaError_t canon_all(double2* z1, double2* Z, double2* zL, int64_t n, int L, int b, cudaStream_t st)
 {
@@ -202,6 +328,33 @@ cudaError_t launch_canonicalize(double2* z1, double2* Z, double2* zL, int64_t n,
     case 10: return canon_all<10>(z1, Z, zL, n, L, b, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+#define BFC_GAUGE_DISPATCH(FN, ...)                 \
+    switch (r) {                                    \
+    case 1: return FN<1>(__VA_ARGS__);              \
+    case 2: return FN<2>(__VA_ARGS__);              \
+    case 3: return FN<3>(__VA_ARGS__);              \
+    case 4: return FN<4>(__VA_ARGS__);              \
+    case 5: return FN<5>(__VA_ARGS__);              \
+    case 6: return FN<6>(__VA_ARGS__);              \
+    case 7: return FN<7>(__VA_ARGS__);              \
+    case 8: return FN<8>(__VA_ARGS__);              \
+    case 9: return FN<9>(__VA_ARGS__);              \
+    case 10: return FN<10>(__VA_ARGS__);            \
+    default: return cudaErrorInvalidValue;          \
+    }
+
+cudaError_t launch_canon_level(double2* z1, double2* Z, double2* zL, int64_t n, int L, int b, int r, int level,
+                               cudaStream_t st)
+{
+    BFC_GAUGE_DISPATCH(canon_one, z1, Z, zL, n, L, b, level, st)
+}
+
+cudaError_t launch_rl_orthogonalize(double2* z1, double2* Z, double2* zL, int64_t n, int L, int b, int r,
+                                    cudaStream_t st)
+{
+    BFC_GAUGE_DISPATCH(rl_all, z1, Z, zL, n, L, b, st)
 }
 
 }  // namespace bfc

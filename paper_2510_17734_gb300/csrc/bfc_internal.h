@@ -88,6 +88,10 @@ struct Ctx {
     int64_t graph_launches = 0;     // kernels in the captured sweep
     bool graph_tc = false;          // Gram kernel the capture used
 
+    // ADAM moments (bfc_adam), packed like the factors, allocated on first use
+    double2* adam_m = nullptr;
+    double2* adam_v = nullptr;
+
     // failure injection of the tests (bfc_inject_fault): 0 off, 1 bulk copies
     // of the solve and gradient kernels not issued (their bounded waits
     // expire), 2 the device error word set on the host before the status read

@@ -44,6 +44,29 @@ void launch_embed(const double2* A, const double2* B, int64_t n, int R, int r, i
                   double2* Z, double2* zL, cudaStream_t st);
 
 // Left-orthogonal gauge of the FP64 factors (bfc_gauge.cu).
+// Randomized low-rank to butterfly conversion (Alg. 2, bfc_lr2bf.cu): the
+// Gaussian count it reads (O_0, then the left and right levels), its scratch
+// size and the launch sequence into the FP64 factors.
+inline int64_t lr2bf_gaussian_count(int64_t n, int L, int b, int r, int p)
+{
+    const int H = L / 2;
+    int64_t rows = n;
+    for (int l = 1; l <= H; ++l) rows += (int64_t)b << (L - l);
+    for (int l = 1; l <= L - H; ++l) rows += (int64_t)b << (L - l);
+    return rows * (r + p);
+}
+size_t lr2bf_scratch_bytes(int64_t n, int L, int b, int R, int r, int p);
+cudaError_t lr2bf_run(const double2* A, const double2* B, const double2* Gs, int64_t n, int L, int b, int R, int r,
+                      int p, double2* z1, double2* Z, double2* zL, void* scratch, cudaStream_t st);
+
+// One level of it (0 = the leaf blocks of z1, m = 1..L = the slice pairs of
+// S^{m+1}); ADF (Alg. 5) moves the orthogonality centre with it.
+cudaError_t launch_canon_level(double2* z1, double2* Z, double2* zL, int64_t n, int L, int b, int r, int level,
+                               cudaStream_t st);
+// Right-to-left orthogonalization (App. A.3, mirrored): every factor but z1
+// right-orthonormal, entries unchanged.
+cudaError_t launch_rl_orthogonalize(double2* z1, double2* Z, double2* zL, int64_t n, int L, int b, int r,
+                                    cudaStream_t st);
 cudaError_t launch_canonicalize(double2* z1, double2* Z, double2* zL, int64_t n, int L, int b, int r,
                                 cudaStream_t st);
 

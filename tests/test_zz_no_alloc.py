@@ -108,11 +108,14 @@ def test_noalloc_rejects_oversize_bad_sizes_and_bad_pointers():
     t1 = torch.zeros(2, dtype=torch.float64, device=dev)
     with pytest.raises(bfc.BfcError, match="EINVAL"):
         bfc.bfc_residual_noalloc(100, 4, 16, 4, F, one, one, t1, sums)
-    with pytest.raises(bfc.BfcError, match="rank"):
-        bfc.bfc_residual_noalloc(n, L, b, 11, F, one, one, t1, sums)
-    # through the C ABI directly (the binding's own checks bypassed): a host
-    # pointer and a factor vector that is only 8-byte aligned are refused
+    # through the C ABI directly (the binding's own checks bypassed): a rank
+    # outside [1, 10], a host pointer and a factor vector that is only
+    # 8-byte aligned are refused
     lib = bfc.load()
+    st = lib.bfc_residual_noalloc(n, L, b, 11, ctypes.c_void_p(F.data_ptr()), 1,
+                                  ctypes.c_void_p(one.data_ptr()), ctypes.c_void_p(one.data_ptr()),
+                                  ctypes.c_void_p(t1.data_ptr()), ctypes.c_void_p(sums.data_ptr()), None)
+    assert st == 1 and "rank" in bfc.bfc_last_error(None)
     host_f = np.zeros(2 * P, dtype=np.float64)
     st = lib.bfc_residual_noalloc(n, L, b, r, host_f.ctypes.data_as(ctypes.c_void_p), 1,
                                   ctypes.c_void_p(one.data_ptr()), ctypes.c_void_p(one.data_ptr()),
