@@ -55,6 +55,16 @@ UNIT = "entries/s"
 WORKLOAD = ("n=65536 L=12 b=16 r=8, exp(i w rho)/rho line-to-line kernel, w=pi n/16, h=1.5, "
             "|Omega|=4 n log2 n (3774874 train / 419430 test), lambda=1e-7")
 TC_FLOPS_PER_ENTRY = 2 * 3 * 128 * 80 * 2   # flop, 2 positions x M 128 x N 80 x 3 products
+# DRAM counters of one k_mid_gram_tc launch (ncu, n = 32768, L = 11: 1,769,472
+# entries, 4096 slices), valid for the kernel source with this sha256 prefix
+TC_GRAM_TRAFFIC = {"source": "paper_2510_17734_gb300/csrc/bfc_gram_tc.cuh", "sha": "9f5dcca506ee0c48",
+                   "read_bytes": 242.100992e6, "write_bytes": 53.273088e6, "entries": 1769472, "slices": 4096}
+
+
+def kernel_source_sha(rel_path: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, rel_path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def load_peaks():
@@ -468,13 +478,101 @@ def run_learned(bfc_mod, n_train=64, n_test=8, epochs=2500, max_sweeps=30, tol=1
     return res
 
 
-def time_oracle_sweep(prob, X0, frac_every: int):
+def run_first_order(bfc_mod, c, prob, hbm_peak, iters=3, nvec=64):
+    """The first-order methods and the matrix-vector product on the bench
+    workload, from the context's current factors: `iters` iterations of ADAM
+    (Alg. 3/4, alpha 1e-3) and of ADF (Alg. 5 with the App. A.3 sweeps), and
+    U = X(S) V for nvec vectors (Eq. butterfly-mat-vec), each timed by the
+    library's per-kernel CUDA events."""
+    X0 = c.get_factors()
+    out = {}
+    for name, run in (("adam", lambda: c.adam(iters, alpha=1e-3)), ("adf", lambda: c.adf(iters))):
+        c.set_factors(X0)
+        c.profile(True)
+        hist = run()
+        prof = c.profile_read()
+        c.profile(False)
+        ms = sum(v[1] for v in prof.values()) / iters
+        out[name] = {"ms_per_iter": ms, "entries_per_s": prob.nnz / (ms * 1e-3),
+                     "train_rel_err": [float(f"{h['train_rel_err']:.4e}") for h in hist],
+                     "kernels_ms": {k: round(v[1] / iters, 4) for k, v in prof.items()}}
+    c.set_factors(X0)
+    V = np.zeros((prob.n, nvec), dtype=np.complex128)
+    V.real = np.random.default_rng(0).standard_normal((prob.n, nvec))
+    c.matvec(V)   # warm-up
+    c.profile(True)
+    c.matvec(V)
+    prof = c.profile_read()
+    c.profile(False)
+    ms = sum(v[1] for v in prof.values())
+    fbytes = c.P * (8 if c.params.prec == bfc_mod.PREC_C64 else 16)
+    by = fbytes + 2 * prob.n * nvec * 16
+    out["matvec"] = {"nvec": nvec, "kernel_ms": ms, "vectors_per_s": nvec / (ms * 1e-3),
+                     "kernels_ms": {k: round(v[1], 4) for k, v in prof.items()},
+                     "roofline": {"bound": "hbm", "bytes": by, "achieved": by / (ms * 1e-3) / 1e9,
+                                  "peak": hbm_peak, "unit": "GB/s", "frac": by / (ms * 1e-3) / 1e9 / hbm_peak,
+                                  "per_unit": "all factors once (compute type) + 16 B per vector entry in and out"}}
+    return out
+
+
+def run_radon(bfc_mod, n=1024, sweeps=20):
+    """The Radon-transform workload of Sec. 5.3 at the paper's Fig. 8 setting:
+    n = 1024, leaf size 4 (L = 8), rank 10, |Omega| = 30 n log2 n (90 % train),
+    lambda = 1e-8, low-rank start of rank 10; ALS sweeps in the precision
+    form and in FP64 on the same GPU."""
+    import synth
+    p = synth.radon_problem(n=n, b=4, r=10, c_obs=30.0, lam=1e-8, sweeps=sweeps)
+    out = {"workload": f"radon n={p.n} L={p.L} b={p.b} r={p.r}, |Omega|=30 n log2 n ({p.nnz} train / "
+                       f"{p.it.size} test), lambda=1e-8, {sweeps} sweeps"}
+    for name, prec in (("precision_form", bfc_mod.PREC_C64), ("plain_fp64", bfc_mod.PREC_FP64)):
+        c = lowrank_start(p, bfc_mod, prec)
+        try:
+            t0 = time.perf_counter()
+            hist = [c.sweep() for _ in range(sweeps)]
+            wall = time.perf_counter() - t0
+        finally:
+            c.close()
+        te = [h["test_rel_err"] for h in hist]
+        out[name] = {"seconds": wall, "ms_per_sweep": 1e3 * wall / sweeps,
+                     "test_rel_err": [float(f"{e:.3e}") for e in te],
+                     "train_rel_err_final": hist[-1]["train_rel_err"]}
+    return out
+
+
+def time_oracle_sweep(prob, X0, frac_every: int, threads: int = 1):
+    """One oracle ALS sweep over every frac_every-th training entry (1 = all
+    of them) on `threads` host threads; returns (entries, seconds)."""
     import oracle
     i, j, t = oracle_sample(prob, frac_every)
-    t0 = time.perf_counter()
-    oracle.als_sweep(prob.n, prob.L, prob.b, prob.r, prob.lam, X0, i, j, t)
-    dt = time.perf_counter() - t0
+    with oracle.threads(threads):
+        t0 = time.perf_counter()
+        oracle.als_sweep(prob.n, prob.L, prob.b, prob.r, prob.lam, X0, i, j, t)
+        dt = time.perf_counter() - t0
     return len(i), dt
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_line(prob, X0):
+    """The oracle on the host: one whole ALS sweep of every training entry on
+    all cores (the OpenMP variant, bit-identical to the serial oracle), and
+    the serial oracle over 1 % and 2 % samples fitted to a whole sweep."""
+    cores = host_cores()
+    mall, tall = time_oracle_sweep(prob, X0, 1, threads=cores)
+    m1, t1 = time_oracle_sweep(prob, X0, 100)
+    m2, t2 = time_oracle_sweep(prob, X0, 50)
+    v1, t_full = oracle_full_rate(prob, m1, t1, m2, t2)
+    return {"value": mall / tall, "unit": UNIT, "cores": cores, "kind": "oracle", "nproc": cores,
+            "sample": f"one whole oracle ALS sweep of all {mall} training entries at the full n=65536 L=12 r=8 "
+                      f"shape on {cores} host threads ({tall:.1f} s; OpenMP over independent systems and "
+                      "entries, bit-identical to the serial oracle)",
+            "serial": {"value": v1, "unit": UNIT, "cores": 1,
+                       "sample": oracle_sample_text(m1, t1, m2, t2, t_full)}}
 
 
 def oracle_full_rate(prob, m1, t1, m2, t2):
@@ -503,24 +601,28 @@ def run_reference(args, rank, world):
     oracle.build()
     prob = synth.config(3)
     X0 = synth.random_factors(prob.n, prob.L, prob.r, prob.seed + synth.SEED_PLANT, sigma=0.3)
+    cores = host_cores()
+    # each step: the oracle (OpenMP variant, all host cores) sweeps a quarter
+    # of the training entries (every 4th) at the full shape, all slices and
+    # fibers solved; warm-up steps sweep 1 %
     for _ in range(args.warmup):
-        time_oracle_sweep(prob, X0, 100)
+        time_oracle_sweep(prob, X0, 100, threads=cores)
     times = []
-    m1 = 0
+    m = 0
     for _ in range(args.steps):
-        m1, dt = time_oracle_sweep(prob, X0, 100)
+        m, dt = time_oracle_sweep(prob, X0, 4, threads=cores)
         times.append(dt)
-    t1 = statistics.mean(times)
-    m2, t2 = time_oracle_sweep(prob, X0, 50)
-    value, t_full = oracle_full_rate(prob, m1, t1, m2, t2)
-    ms = 1e3 * t1
-    sample = ("each step: " + oracle_sample_text(m1, t1, m2, t2, t_full)
-              + "; ms_per_step is the 1% sweep")
+    t_step = statistics.mean(times)
+    value = m / t_step
+    sample = (f"each step: one oracle ALS sweep (complex128, OpenMP variant on {cores} host threads, "
+              f"bit-identical to the serial oracle) over every 4th training entry ({m} entries) at the full "
+              f"n=65536 L=12 r=8 shape, all 98304 slice and 131072 fiber systems solved; {t_step:.2f} s per "
+              "step; warm-up steps sweep 1 %")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": "host, serial"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD, "parallelism": f"host, {cores} threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -650,16 +752,20 @@ def run_bfc(args, rank, world, local_rank):
         # the nominal dense TF32 / BF16 ratio 1.1 / 2.25
         peak_tflops = peaks.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25
         executed = prob.nnz * TC_FLOPS_PER_ENTRY / (mid_avg_ms * 1e-3) / 1e12
-        # DRAM bytes per launch from the ncu capture summarised in
-        # profiles/k_mid_gram_tc_n32768_c64.md (n = 32768, scaled to this
-        # workload by training entries for reads and slices for writes)
+        # DRAM bytes per launch from one ncu capture of this kernel at
+        # n = 32768, scaled to this workload by training entries (reads) and
+        # slices (writes); null once the kernel source differs from the one
+        # the counters were taken on
         traffic = None
-        if not args.n:
-            traffic = 242.374656e6 * prob.nnz / 1769472 + 52.970752e6 * 2
+        cap = TC_GRAM_TRAFFIC
+        if not args.n and kernel_source_sha(cap["source"]) == cap["sha"]:
+            traffic = (cap["read_bytes"] * prob.nnz / cap["entries"]
+                       + cap["write_bytes"] * (1 << (prob.L + 1)) / cap["slices"])
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / peak_tflops, "traffic": traffic,
                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at "
-                                      "n=32768, scaled by entries (reads) and slices (writes)",
+                                      f"n=32768 (kernel source sha {cap['sha']}), scaled by entries (reads) "
+                                      "and slices (writes)",
                     "kernel": "k_mid_gram_tc (tcgen05 per-slice normal equations, one launch per middle level)",
                     "launch_ms": mid_avg_ms, "flop_per_launch": flops_per_launch,
                     "peak_source": "MEASURED_PEAKS bf16_tflops_sustained x 1.1/2.25 (of measured)",
@@ -698,7 +804,18 @@ def run_bfc(args, rank, world, local_rank):
                                    "how": "bfc_measure_alu_peaks: dependent FMA chains on all SMs, best of 5"},
             "clocks": clocks,
             "sweep_stats": {"train_rel_err": stats[-1]["train_rel_err"],
-                            "test_rel_err": stats[-1]["test_rel_err"]}}
+                            "test_rel_err": stats[-1]["test_rel_err"],
+                            "fp64_fallback_fraction": (sum(int(st["refined_fallbacks"]) for st in stats)
+                                                       / (len(stats) * prob.L * (1 << (prob.L + 1)))),
+                            "refine_steps_per_slice": (sum(int(st["refine_steps"]) for st in stats)
+                                                       / (len(stats) * prob.L * (1 << (prob.L + 1))))}}
+
+    if not args.no_first_order:
+        X_keep = c.get_factors()
+        line["first_order"] = run_first_order(bfc, c, prob, load_peaks().get("hbm_gbs", 6800.0))
+        c.set_factors(X_keep)
+    if not args.no_radon and not args.n:
+        line["radon"] = run_radon(bfc)
 
     if not args.no_ttt:
         # the specified workload cannot generalize (|Omega| = 4 n log2 n gives about one
@@ -724,11 +841,7 @@ def run_bfc(args, rank, world, local_rank):
         import oracle
         oracle.build()
         X0 = c.get_factors()
-        m1, t1 = time_oracle_sweep(prob, X0, 100)
-        m2, t2 = time_oracle_sweep(prob, X0, 50)
-        v, t_full = oracle_full_rate(prob, m1, t1, m2, t2)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": oracle_sample_text(m1, t1, m2, t2, t_full)}
+        line["cpu_baseline"] = cpu_baseline_line(prob, X0)
     c.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -746,6 +859,8 @@ def main():
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance runs")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload run")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-start run")
+    ap.add_argument("--no-first-order", action="store_true", help="skip the ADAM / ADF / matvec run")
+    ap.add_argument("--no-radon", action="store_true", help="skip the Radon-transform run")
     ap.add_argument("--learned-train", type=int, default=64, help="training completions of the learned start")
     ap.add_argument("--learned-epochs", type=int, default=2500, help="training epochs of the learned start")
     ap.add_argument("--gram", default="tensor", choices=["tensor", "cuda"],

@@ -239,12 +239,12 @@ def matvec(n, L, b, r, packed, V):
     return U.ravel() if one else U
 
 
-def lr_complete(n, R, lam, A0, B0, i, j, t, sweeps):
+def lr_complete(n, R, lam, A0, B0, i, j, t, sweeps, ridge_rel=0.0):
     """Low-rank matrix completion = Alg. 1 with L = 0 (leaf size n).
     Returns (A, B) with X = A B^T."""
     packed = np.concatenate([_c128(A0).ravel(), _c128(B0).ravel()])
     for _ in range(sweeps):
-        packed, _st = als_sweep(n, 0, n, R, lam, packed, i, j, t)
+        packed, _st = als_sweep(n, 0, n, R, lam, packed, i, j, t, ridge_rel=ridge_rel)
     return packed[:n * R].reshape(n, R), packed[n * R:].reshape(n, R)
 
 

@@ -363,6 +363,7 @@ k_adf_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>::
     __shared__ V w_s[CH * R];
     __shared__ V g_s[CH];
     __shared__ double2 n_s[D];
+    __shared__ V nt_s[D];   // the direction in the compute type, for the per-entry products
     __shared__ double red[4];
     __shared__ double alpha_s;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -374,21 +375,17 @@ k_adf_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>::
         __syncthreads();
         return red[0] + red[1] + red[2] + red[3];
     };
+    // z_e = h^T N w in the compute type (the entry's own precision)
     auto zval = [&](const V (&h)[R], const V (&w)[R]) {
-        double zx = 0.0, zy = 0.0;
+        V z = czero<V>();
 #pragma unroll
         for (int a = 0; a < R; ++a) {
-            double tx = 0.0, ty = 0.0;   // (N w)_a
+            V nw = czero<V>();   // (N w)_a
 #pragma unroll
-            for (int c = 0; c < R; ++c) {
-                const double2 nv = n_s[a * R + c];
-                tx += nv.x * (double)w[c].x - nv.y * (double)w[c].y;
-                ty += nv.x * (double)w[c].y + nv.y * (double)w[c].x;
-            }
-            zx += (double)h[a].x * tx - (double)h[a].y * ty;
-            zy += (double)h[a].x * ty + (double)h[a].y * tx;
+            for (int c = 0; c < R; ++c) cmac(nw, nt_s[a * R + c], w[c]);
+            cmac(z, h[a], nw);
         }
-        return make_double2(zx, zy);
+        return to_d2(z);
     };
     for (int k = blockIdx.x; k < S; k += gridDim.x) {
         const int s0 = seg[k], s1 = seg[k + 1];
@@ -425,6 +422,7 @@ k_adf_mid(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>::
                 const double2 sd = Zd[(size_t)k * D + q];
                 const double2 nv = make_double2(nq[u].x - lam * sd.x, nq[u].y - lam * sd.y);
                 n_s[q] = nv;
+                nt_s[q] = from_d2<V>(nv);
                 nn += nv.x * nv.x + nv.y * nv.y;
             }
         }

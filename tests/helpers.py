@@ -62,3 +62,39 @@ def rel_dev(x, ref):
     rms = math.sqrt(float(np.mean(np.abs(ref) ** 2))) if ref.size else 1.0
     den = np.maximum(np.abs(ref), rms if rms > 0 else 1.0)
     return float(np.max(np.abs(x - ref) / den)) if ref.size else 0.0
+
+
+def block_conditions(X0, X1, i, j, t, n, L, b, r, lam, ridge_rel=0.0):
+    """Condition numbers of every block system K + lambda_eff I of one ALS
+    sweep from X0 that produced X1 (Alg. 1 order: each level's design from the
+    new factors left of it and the old factors right of it), with
+    lambda_eff = max(lam, ridge_rel trace(K) / dim).  Returns a list with one
+    array of condition numbers per level (S^1, the middle factors, S^{L+2})."""
+    z1o, Zo, zLo = split_packed(X0, n, L, b, r)
+    z1n, Zn, zLn = split_packed(X1, n, L, b, r)
+    i, j = np.asarray(i), np.asarray(j)
+
+    def cond(A):
+        K = A.conj().T @ A
+        d = K.shape[0]
+        le = max(lam, ridge_rel * float(np.trace(K).real) / d)
+        ev = np.linalg.eigvalsh(K + le * np.eye(d))
+        return float(ev[-1] / ev[0]) if ev[0] > 0 else float("inf")
+
+    out = []
+    _, w_old = envs_numpy(z1o, Zo, zLo, i, j, L, b, r)
+    out.append(np.array([cond(w_old[0][i == row]) for row in range(n) if np.any(i == row)]))
+    pi, pj = i // b, j // b
+    for m in range(1, L + 1):
+        Zmix = np.concatenate([Zn[: m - 1], Zo[m - 1:]])
+        h_new, _ = envs_numpy(z1n, Zmix, zLo, i, j, L, b, r)
+        key = ((pi >> (m - 1)) << m) | (pj >> (L - m))
+        cs = []
+        for k in np.unique(key):
+            sel = key == k
+            A = np.einsum("ea,ec->eac", h_new[m][sel], w_old[m][sel]).reshape(int(sel.sum()), r * r)
+            cs.append(cond(A))
+        out.append(np.array(cs))
+    h_new, _ = envs_numpy(z1n, Zn, zLo, i, j, L, b, r)
+    out.append(np.array([cond(h_new[L + 1][j == col]) for col in range(n) if np.any(j == col)]))
+    return out

@@ -1,0 +1,104 @@
+"""Full-size parity with the oracle's stored trajectories.
+
+tests/golden/oracle_sweeps_*.txt hold the complex128 oracle's per-sweep
+training and test errors (Eq. BF_convergence) and objectives, written by
+tests/golden/make_oracle_sweeps.py (oracle and synth only), from the
+oracle's low-rank start (Alg. 1 with L = 0, R = r, 10 sweeps, exact
+embedding).  The test recomputes that start with the oracle, hands it to the
+GPU and runs the same sweeps:
+
+* cfg3: n = 65536, L = 12, r = 8, |Omega| = 4 n log2 n (the benchmark
+  workload; about one observation per free parameter, so the test error
+  rises while the training error falls);
+* rule16k: the same operator family at n = 16384 with the paper's sampling
+  rule 6 r n log2 n, where ALS reaches test error 3e-4 in four sweeps.
+
+FP64 path: every sweep's errors and objective within 1e-8 relative of the
+oracle's.  Precision form: the final test error within 1e-4 absolute of the
+oracle's on the rule16k workload (the target of the precision form); on cfg3
+every sweep's training error within 1e-4 relative.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2510_17734_gb300 as bfc
+import synth
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys_path_golden = os.path.join(HERE, "golden")
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(sys_path_golden, f"oracle_sweeps_{name}.txt")) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                s, tr, te, ob = ln.split()
+                rows.append((int(s), float(tr), float(te), float(ob)))
+    return rows
+
+
+def _problem(name):
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_oracle_sweeps",
+                                                  os.path.join(sys_path_golden, "make_oracle_sweeps.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    make, _, _ = mod.WORKLOADS[name]
+    p = make()
+    with oracle.threads(oracle.max_threads()):
+        X0 = mod.oracle_start(p)
+    return p, X0
+
+
+@pytest.fixture(scope="module")
+def cfg3():
+    return _problem("cfg3")
+
+
+@pytest.fixture(scope="module")
+def rule16k():
+    return _problem("rule16k")
+
+
+def _run(p, X0, prec, sweeps):
+    with bfc.Completion(p.n, p.L, p.b, p.r, p.lam, p.i, p.j, p.t, p.it, p.jt, p.tt, prec=prec) as c:
+        c.set_factors(X0)
+        return [c.sweep() for _ in range(sweeps)]
+
+
+@pytest.mark.parametrize("name", ["cfg3", "rule16k"])
+def test_fp64_trajectory_matches_oracle(request, name):
+    p, X0 = request.getfixturevalue(name)
+    gold = _golden(name)
+    start = gold[0]
+    assert abs(oracle.rel_err(p.n, p.L, p.b, p.r, X0, p.it, p.jt, p.tt) - start[2]) <= 1e-12 * start[2]
+    hist = _run(p, X0, bfc.PREC_FP64, len(gold) - 1)
+    for h, (s, tr, te, ob) in zip(hist, gold[1:]):
+        assert abs(h["train_rel_err"] - tr) <= 1e-8 * tr, (s, h["train_rel_err"], tr)
+        assert abs(h["test_rel_err"] - te) <= 1e-8 * te, (s, h["test_rel_err"], te)
+        assert abs(h["objective"] - ob) <= 1e-8 * ob, (s, h["objective"], ob)
+
+
+def test_precision_form_final_test_error_within_1e4(rule16k):
+    p, X0 = rule16k
+    gold = _golden("rule16k")
+    hist = _run(p, X0, bfc.PREC_C64, len(gold) - 1)
+    final_gpu, final_oracle = hist[-1]["test_rel_err"], gold[-1][2]
+    assert abs(final_gpu - final_oracle) <= 1e-4, (final_gpu, final_oracle)
+    # and the sweep at which the test error first falls below 1e-3 is the same
+    first = lambda errs: next((q for q, e in enumerate(errs) if e < 1e-3), None)  # noqa: E731
+    assert first([h["test_rel_err"] for h in hist]) == first([g[2] for g in gold[1:]])
+
+
+def test_precision_form_training_errors_follow_oracle_at_full_size(cfg3):
+    p, X0 = cfg3
+    gold = _golden("cfg3")
+    hist = _run(p, X0, bfc.PREC_C64, len(gold) - 1)
+    for h, (s, tr, te, ob) in zip(hist, gold[1:]):
+        assert abs(h["train_rel_err"] - tr) <= 1e-4 * tr, (s, h["train_rel_err"], tr)
