@@ -160,7 +160,7 @@ def job_throughput(units_per_rank: int, world: int, ms_step: float) -> float:
     return world * units_per_rank / (ms_step * 1e-3)
 
 
-def kernel_rooflines(prob, prof, stats, peaks, fp32_meas, main_roof):
+def kernel_rooflines(prob, prof, stats, peaks, fp32_meas):
     """Per-kernel algorithmic work against the measured peaks (complex64
     precision form), from the library's CUDA-event timers of the timed sweeps.
 
@@ -189,17 +189,6 @@ def kernel_rooflines(prob, prof, stats, peaks, fp32_meas, main_roof):
         out.append({"kernel": "k_env_right", "bound": "hbm", "launch_ms": ms, "bytes": by,
                     "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
                     "per_unit": f"{16 * r + 4} B per entry (w in, w out, level map) + {D * 8} B per slice"})
-    ms = avg_ms("mid_gram")
-    if ms:
-        fl = nnz * als_flops_per_entry(r)
-        a = fl / (ms * 1e-3) / 1e12
-        out.append({"kernel": main_roof["kernel"].split(" ")[0], "bound": main_roof["bound"],
-                    "launch_ms": ms, "flop": fl, "achieved": a, "unit": "TFLOP/s",
-                    "peak": main_roof["peak"], "frac": main_roof["frac"],
-                    "fp32_peak": fp32_meas, "fp32_frac": a / fp32_meas,
-                    "per_unit": f"{als_flops_per_entry(r)} flop per entry (Hermitian Gram + right-hand side)",
-                    "note": "fp32_frac: the same complex64-accurate contraction against the measured "
-                            "FP32 FMA peak of the CUDA cores"})
     ms = avg_ms("mid_solve")
     if ms:
         by = S * (npk + D) * 8 + nnz * (16 * r + 4) + S * D * 24 + 4 * (S + 1)
@@ -237,6 +226,97 @@ def kernel_rooflines(prob, prof, stats, peaks, fp32_meas, main_roof):
                     "achieved": af, "peak": fp32_meas, "unit": "TFLOP/s", "frac": af / fp32_meas,
                     "per_unit": f"{8 * (L * D + 2 * r)} flop per test entry (L r x r complex products)",
                     "note": "thread per test entry; the slices come from L2 (factors fit in it)"})
+    keymap = {"k_env_right": "env_right", "k_mid_solve": "mid_solve", "k_outer_gram (rows)": "outer_rows_gram",
+              "k_outer_gram (columns)": "outer_cols_gram", "k_outer_post (rows)": "outer_rows_post",
+              "k_outer_post (columns)": "outer_cols_post", "k_eval": "eval"}
+    for o in out:
+        o["ms_per_sweep"] = prof.get(keymap[o["kernel"]], (0, 0.0))[1] / max(len(stats), 1)
+        o.setdefault("traffic", None)
+    return out
+
+
+def group_counts(prob):
+    """Row / column groups of every middle level, by the library's rule:
+    inside a slice of S^{m+1}, the entries of one row (levels with
+    2m <= L + 1) or of one column share an environment."""
+    pi, pj = prob.i.astype(np.int64) // prob.b, prob.j.astype(np.int64) // prob.b
+    out = {}
+    for m in range(1, prob.L + 1):
+        k = ((pi >> (m - 1)) << m) | (pj >> (prob.L - m))
+        by_col = 2 * m > prob.L + 1
+        other = prob.j if by_col else prob.i
+        out[m] = int(np.unique(k * prob.n + other).size)
+    return out
+
+
+def gram_rooflines(prob, prof, n_sweeps, c64, tc_levels, auto, peaks, fp32_meas, fp64_meas, args):
+    """Rooflines of the middle-level normal-equation kernels of the timed
+    sweeps: the per-entry kernel (tensor cores, or CUDA cores) at the levels
+    it ran, and the grouped CUDA-core kernel at the levels with few row /
+    column groups (algorithmic flops: 8 (D(D+1)/2 + D) per group for the
+    Kronecker updates plus 8 (r^2 + r) per entry for the group sums)."""
+    r, nnz = prob.r, prob.nnz
+    D = r * r
+    out = []
+    groups = group_counts(prob) if auto and r in (4, 8) else {}
+    ratio = 0.45 if tc_levels else 0.9
+    grouped = {m: g for m, g in groups.items() if g < ratio * nnz}
+    n_plain = prob.L - len(grouped)
+    cnt, tot = prof.get("mid_gram", (0, 0.0))
+    if cnt and n_plain:
+        ms = tot / cnt
+        fl = nnz * als_flops_per_entry(r)
+        a = fl / (ms * 1e-3) / 1e12
+        if tc_levels:
+            # tcgen05 kind::tf32: the measured sustained bf16 peak (the kernel
+            # runs inside a long step) times the nominal dense TF32 / BF16
+            # ratio 1.1 / 2.25
+            peak = peaks.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25
+            executed = nnz * TC_FLOPS_PER_ENTRY / (ms * 1e-3) / 1e12
+            traffic = None
+            cap = TC_GRAM_TRAFFIC
+            if not args.n and kernel_source_sha(cap["source"]) == cap["sha"]:
+                traffic = (cap["read_bytes"] * nnz / cap["entries"]
+                           + cap["write_bytes"] * (1 << (prob.L + 1)) / cap["slices"])
+            out.append({"kernel": "k_mid_gram_tc", "bound": "tensor", "achieved": a, "peak": peak,
+                        "unit": "TFLOP/s", "frac": a / peak, "traffic": traffic,
+                        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at "
+                                          f"n=32768 (kernel source sha {cap['sha']}), scaled by entries (reads) "
+                                          "and slices (writes)",
+                        "launch_ms": ms, "launches_per_sweep": n_plain, "ms_per_sweep": tot / n_sweeps,
+                        "flop_per_launch": fl,
+                        "per_unit": f"{als_flops_per_entry(r)} flop per entry (Hermitian Gram + right-hand side)",
+                        "peak_source": "MEASURED_PEAKS bf16_tflops_sustained x 1.1/2.25 (of measured)",
+                        "executed_tflops": executed, "executed_frac": executed / peak,
+                        "executed_note": "issued MMA flops: 128 x 80 real embedding of the complex Gram "
+                                         "(Re and Im, full square, 2 contraction positions per entry) x 3 TF32 "
+                                         "split products = 122880 flop per entry",
+                        "fp32_peak": fp32_meas, "fp32_frac": a / fp32_meas})
+        else:
+            peak = fp32_meas if c64 else fp64_meas
+            out.append({"kernel": "k_mid_gram", "bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s",
+                        "frac": a / peak, "traffic": None, "launch_ms": ms, "launches_per_sweep": n_plain,
+                        "ms_per_sweep": tot / n_sweeps, "flop_per_launch": fl,
+                        "per_unit": f"{als_flops_per_entry(r)} flop per entry",
+                        "peak_source": ("measured FP32" if c64 else "measured FP64") +
+                                       " FMA-chain peak (bfc_measure_alu_peaks, of measured)"})
+    cnt, tot = prof.get("mid_gram_grp", (0, 0.0))
+    if cnt and grouped:
+        ms = tot / cnt
+        per_group = 8 * (D * (D + 1) // 2 + D)
+        per_entry = 8 * (D + r)
+        fl = (sum(grouped.values()) * per_group + len(grouped) * nnz * per_entry) / len(grouped)
+        a = fl / (ms * 1e-3) / 1e12
+        peak = fp32_meas if c64 else fp64_meas
+        out.append({"kernel": "k_mid_gram_grp", "bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s",
+                    "frac": a / peak, "traffic": None, "launch_ms": ms, "launches_per_sweep": len(grouped),
+                    "ms_per_sweep": tot / n_sweeps, "flop_per_launch": fl,
+                    "groups_per_level": grouped,
+                    "per_unit": f"{per_group} flop per row / column group (Kronecker update of the Hermitian "
+                                f"Gram + right-hand side) + {per_entry} flop per entry (group sums)",
+                    "peak_source": ("measured FP32" if c64 else "measured FP64") +
+                                   " FMA-chain peak (bfc_measure_alu_peaks, of measured)",
+                    "per_entry_equivalent_tflops": nnz * als_flops_per_entry(r) / (ms * 1e-3) / 1e12})
     return out
 
 
@@ -515,27 +595,30 @@ def run_first_order(bfc_mod, c, prob, hbm_peak, iters=3, nvec=64):
     return out
 
 
-def run_radon(bfc_mod, n=1024, sweeps=20):
-    """The Radon-transform workload of Sec. 5.3 at the paper's Fig. 8 setting:
-    n = 1024, leaf size 4 (L = 8), rank 10, |Omega| = 30 n log2 n (90 % train),
-    lambda = 1e-8, low-rank start of rank 10; ALS sweeps in the precision
-    form and in FP64 on the same GPU."""
+def run_radon(bfc_mod, sweeps=20, fp64_sweeps=2):
+    """The Radon-transform workload of Sec. 5.3 at the paper's convergence
+    study: n = 4096, leaf size 4 (L = 10), rank 10, 7 r n log2 n training and
+    r n log2 n test entries, lambda = 1e-8, low-rank start of rank 10; ALS
+    sweeps in the precision form, and the first sweeps in plain FP64 on the
+    same GPU for the time per sweep."""
     import synth
-    p = synth.radon_problem(n=n, b=4, r=10, c_obs=30.0, lam=1e-8, sweeps=sweeps)
-    out = {"workload": f"radon n={p.n} L={p.L} b={p.b} r={p.r}, |Omega|=30 n log2 n ({p.nnz} train / "
-                       f"{p.it.size} test), lambda=1e-8, {sweeps} sweeps"}
-    for name, prec in (("precision_form", bfc_mod.PREC_C64), ("plain_fp64", bfc_mod.PREC_FP64)):
+    p = synth.radon_problem(sweeps=sweeps)
+    out = {"workload": f"radon n={p.n} L={p.L} b={p.b} r={p.r}, |Omega|=7 r n log2 n ({p.nnz} train / "
+                       f"{p.it.size} test), lambda=1e-8, low-rank start (rank 10, 10 sweeps)"}
+    for name, prec, ns in (("precision_form", bfc_mod.PREC_C64, sweeps), ("plain_fp64", bfc_mod.PREC_FP64,
+                                                                          fp64_sweeps)):
         c = lowrank_start(p, bfc_mod, prec)
         try:
             t0 = time.perf_counter()
-            hist = [c.sweep() for _ in range(sweeps)]
+            hist = [c.sweep() for _ in range(ns)]
             wall = time.perf_counter() - t0
         finally:
             c.close()
         te = [h["test_rel_err"] for h in hist]
-        out[name] = {"seconds": wall, "ms_per_sweep": 1e3 * wall / sweeps,
+        first = next((q + 1 for q, e in enumerate(te) if e < 1e-3), None)
+        out[name] = {"sweeps": ns, "seconds": wall, "ms_per_sweep": 1e3 * wall / ns,
                      "test_rel_err": [float(f"{e:.3e}") for e in te],
-                     "train_rel_err_final": hist[-1]["train_rel_err"]}
+                     "train_rel_err_final": hist[-1]["train_rel_err"], "first_sweep_below_1e-3": first}
     return out
 
 
@@ -648,7 +731,8 @@ def run_bfc(args, rank, world, local_rank):
         f"(profiling case, {prob.nnz} train entries)")
     prec = bfc.PREC_C64 if args.prec == "c64" else bfc.PREC_FP64
 
-    c = lowrank_start(prob, bfc, prec, gram=bfc.GRAM_TENSOR if args.gram == "tensor" else bfc.GRAM_CUDA)
+    c = lowrank_start(prob, bfc, prec, gram={"auto": bfc.GRAM_AUTO, "tensor": bfc.GRAM_TENSOR,
+                                             "cuda": bfc.GRAM_CUDA}[args.gram])
     stream = torch.cuda.Stream(device=dev)
     bfc.bfc_set_stream(c.ctx, stream.cuda_stream)
 
@@ -734,58 +818,21 @@ def run_bfc(args, rank, world, local_rank):
                 "note": "one full gradient (all factors) per call, device-resident; call_ms includes the "
                         "host synchronisation for the objective"}
 
-    # roofline of the dominant kernel (per-slice normal equations + solve)
+    # rooflines of the normal-equation kernels and of the others; the line's
+    # "roofline" is the kernel with the most device time per sweep
     launches = sum(int(st["launches"]) for st in stats)   # kernels launched by the timed sweeps
-    mid_n, mid_ms = prof.get("mid_gram", (0, 0.0))
-    if mid_n == 0 or mid_ms <= 0.0:
-        raise RuntimeError(f"no timing for the normal-equation kernel in the profile: {sorted(prof)}")
-    mid_avg_ms = mid_ms / mid_n
-    flops_per_launch = prob.nnz * als_flops_per_entry(prob.r)
     clocks = clk.summary()
     peaks = load_peaks()
     fp32_meas, fp64_meas = bfc.bfc_measure_alu_peaks()
-    achieved = flops_per_launch / (mid_avg_ms * 1e-3) / 1e12
-    tensor_gram = prec == bfc.PREC_C64 and args.gram == "tensor" and prob.r <= 8
-    if tensor_gram:
-        # tcgen05 kind::tf32: the contraction's own peak is the measured
-        # sustained bf16 peak (the kernel runs inside a long step) scaled by
-        # the nominal dense TF32 / BF16 ratio 1.1 / 2.25
-        peak_tflops = peaks.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25
-        executed = prob.nnz * TC_FLOPS_PER_ENTRY / (mid_avg_ms * 1e-3) / 1e12
-        # DRAM bytes per launch from one ncu capture of this kernel at
-        # n = 32768, scaled to this workload by training entries (reads) and
-        # slices (writes); null once the kernel source differs from the one
-        # the counters were taken on
-        traffic = None
-        cap = TC_GRAM_TRAFFIC
-        if not args.n and kernel_source_sha(cap["source"]) == cap["sha"]:
-            traffic = (cap["read_bytes"] * prob.nnz / cap["entries"]
-                       + cap["write_bytes"] * (1 << (prob.L + 1)) / cap["slices"])
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tflops, "traffic": traffic,
-                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at "
-                                      f"n=32768 (kernel source sha {cap['sha']}), scaled by entries (reads) "
-                                      "and slices (writes)",
-                    "kernel": "k_mid_gram_tc (tcgen05 per-slice normal equations, one launch per middle level)",
-                    "launch_ms": mid_avg_ms, "flop_per_launch": flops_per_launch,
-                    "peak_source": "MEASURED_PEAKS bf16_tflops_sustained x 1.1/2.25 (of measured)",
-                    "executed_tflops": executed, "executed_frac": executed / peak_tflops,
-                    "executed_note": "issued MMA flops: 128 x 80 real embedding of the complex Gram "
-                                     "(Re and Im, full square, 2 contraction positions per entry) x 3 TF32 "
-                                     "split products = 122880 flop per entry"}
-    else:
-        fp64_path = prec != bfc.PREC_C64
-        peak_tflops = fp64_meas if fp64_path else fp32_meas
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tflops, "traffic": None,
-                    "kernel": "k_mid_gram (per-slice normal equations, one launch per middle level)",
-                    "launch_ms": mid_avg_ms, "flop_per_launch": flops_per_launch,
-                    "peak_source": ("measured FP64" if fp64_path else "measured FP32") +
-                                   " FMA-chain peak (bfc_measure_alu_peaks, of measured)"}
-
-    kernel_roof = kernel_rooflines(prob, prof, stats, peaks, fp32_meas, roofline) \
-        if prec == bfc.PREC_C64 else None
-
+    n_sweeps = max(args.steps, 1)
+    tc_levels = prec == bfc.PREC_C64 and args.gram != "cuda" and prob.r <= 8
+    entries = gram_rooflines(prob, prof, n_sweeps, prec == bfc.PREC_C64, tc_levels, args.gram == "auto",
+                             peaks, fp32_meas, fp64_meas, args)
+    entries += kernel_rooflines(prob, prof, stats, peaks, fp32_meas) if prec == bfc.PREC_C64 else []
+    if not entries:
+        raise RuntimeError(f"no kernel timings in the profile: {sorted(prof)}")
+    roofline = dict(max(entries, key=lambda x: x["ms_per_sweep"]))
+    kernel_roof = entries
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64+f64" if prec == bfc.PREC_C64 else "f64",
@@ -863,8 +910,10 @@ def main():
     ap.add_argument("--no-radon", action="store_true", help="skip the Radon-transform run")
     ap.add_argument("--learned-train", type=int, default=64, help="training completions of the learned start")
     ap.add_argument("--learned-epochs", type=int, default=2500, help="training epochs of the learned start")
-    ap.add_argument("--gram", default="tensor", choices=["tensor", "cuda"],
-                    help="precision-form middle-level Gram: tcgen05 tensor cores or CUDA cores")
+    ap.add_argument("--gram", default="auto", choices=["auto", "tensor", "cuda"],
+                    help="middle-level Gram: auto (grouped CUDA-core kernel at levels with few row / column "
+                         "groups, tcgen05 per entry elsewhere), tensor (tcgen05 per entry), cuda (CUDA cores "
+                         "per entry)")
     ap.add_argument("--n", type=int, default=0,
                     help="reduced n with the same construction (small profiling captures only)")
     args = ap.parse_args()

@@ -26,7 +26,7 @@ __all__ = [
     "bfc_eval", "bfc_als_sweep", "bfc_grad", "bfc_lowrank_init", "bfc_complete",
     "bfc_profile_enable", "bfc_profile_read", "bfc_last_error", "bfc_destroy",
     "bfc_decode", "bfc_get_order", "bfc_residual_noalloc", "bfc_lbfgs", "bfc_batch_complete",
-    "batch_complete", "GRAM_TENSOR", "GRAM_CUDA",
+    "batch_complete", "GRAM_AUTO", "GRAM_TENSOR", "GRAM_CUDA",
     "bfc_mlp_create", "bfc_mlp_dims", "bfc_mlp_num_params", "bfc_mlp_get_params", "bfc_mlp_set_params",
     "bfc_mlp_set_scaling", "bfc_mlp_forward", "bfc_mlp_grad", "bfc_mlp_train", "bfc_mlp_destroy",
     "bfc_init_learned", "bfc_canonicalize", "Mlp", "bfc_measure_alu_peaks", "bfc_inject_fault",
@@ -35,8 +35,9 @@ __all__ = [
 
 PREC_FP64 = 0
 PREC_C64 = 1
-GRAM_TENSOR = 0   # tcgen05 Gram for r <= 8 in the precision form
-GRAM_CUDA = 1     # CUDA-core Gram always
+GRAM_AUTO = 0     # per middle level: grouped CUDA-core Gram where few row / column groups, else tcgen05 (r <= 8)
+GRAM_CUDA = 1     # CUDA-core Gram per entry always
+GRAM_TENSOR = 2   # tcgen05 Gram per entry for r <= 8 in the precision form, no grouping
 STATUS = {0: "BFC_OK", 1: "BFC_EINVAL", 2: "BFC_ENOMEM", 3: "BFC_ECUDA", 4: "BFC_ESINGULAR",
           5: "BFC_ETIMEOUT", 6: "BFC_ENONFINITE"}
 
@@ -503,7 +504,7 @@ class Completion:
 
     def __init__(self, n, L, b, r, lam, i, j, t, it=None, jt=None, tt=None, prec=PREC_FP64,
                  max_sweeps=20, tol=1e-3, seed=0, init_kind=0, lr_rank=0, lr_sweeps=10,
-                 refine_sweeps=0, ridge_rel=0.0, gram_impl=GRAM_TENSOR, lr2bf_oversample=0):
+                 refine_sweeps=0, ridge_rel=0.0, gram_impl=GRAM_AUTO, lr2bf_oversample=0):
         self.n, self.L, self.b, self.r = int(n), int(L), int(b), int(r)
         self.params = Params(n=n, L=L, b=b, r=r, lam=lam, prec=prec, max_sweeps=max_sweeps, tol=tol,
                              seed=seed, init_kind=init_kind, lr_rank=lr_rank, lr_sweeps=lr_sweeps,

@@ -237,13 +237,53 @@ static bfc_status build(Ctx* c, const Inputs& in)
     c->tval.assign(NL, nullptr);
     c->nxt.assign(L + 1, nullptr);
     c->prv.assign(L + 1, nullptr);
+    c->grp.assign(NL, GroupLevel{});
+    std::vector<uint32_t> hkeys;
     for (int l = 0; l < NL; ++l) {
         const int64_t K = (l == 0 || l == L + 1) ? n : S;
         BFC_TRY(dalloc(c, (void**)&perm[l], N * 4, "perm"));
         BFC_TRY(tmp((void**)&pos[l], N * 4, "pos"));
         BFC_TRY(dalloc(c, (void**)&c->seg[l], (K + 1) * 4, "segments"));
         BFC_TRY(dalloc(c, &c->tval[l], N * c->vsz, "level values"));
-        BFC_CK(c, sort_level(c->d_i, c->d_j, N, l, L, c->b, K, c->stream, ss, perm[l], c->seg[l]));
+        // middle levels: inside a slice, entries of one row (levels m with
+        // 2m <= L+1, where a slice's block has fewer rows than columns) or of
+        // one column are contiguous; they share h_m (resp. w_m)
+        int64_t loc = 0;
+        int by_col = 0;
+        if (l >= 1 && l <= L) {
+            by_col = 2 * l > L + 1;
+            loc = by_col ? ((int64_t)c->b << (L - l)) : ((int64_t)c->b << (l - 1));
+            if ((double)S * (double)loc >= 2147483647.0) loc = 0;
+        }
+        uint32_t* skeys = nullptr;
+        BFC_CK(c, sort_level(c->d_i, c->d_j, N, l, L, c->b, K, loc, by_col, c->stream, ss, perm[l], c->seg[l],
+                             &skeys));
+        if (loc > 0) {
+            // row / column groups of the level: entry offsets and the first
+            // group of every slice
+            hkeys.resize(N);
+            BFC_CK(c, cudaMemcpyAsync(hkeys.data(), skeys, N * 4, cudaMemcpyDeviceToHost, c->stream));
+            BFC_TRY(sync(c));
+            std::vector<int32_t> gst, gsg(S + 1, 0);
+            gst.reserve(N / 2 + 1);
+            for (int64_t p = 0; p < N; ++p)
+                if (p == 0 || hkeys[p] != hkeys[p - 1]) gst.push_back((int32_t)p);
+            const int64_t G = (int64_t)gst.size();
+            gst.push_back((int32_t)N);
+            int64_t g = 0;
+            for (int64_t k = 0; k <= S; ++k) {
+                while (g < G && (int64_t)(hkeys[gst[g]] / (uint64_t)loc) < k) ++g;
+                gsg[k] = (int32_t)g;
+            }
+            GroupLevel& gl = c->grp[l];
+            gl.by_col = by_col;
+            gl.ngroups = G;
+            BFC_TRY(dalloc(c, (void**)&gl.gstart, (size_t)(G + 1) * 4, "group offsets"));
+            BFC_TRY(dalloc(c, (void**)&gl.gseg, (size_t)(S + 1) * 4, "slice group offsets"));
+            BFC_CK(c, cudaMemcpyAsync(gl.gstart, gst.data(), (size_t)(G + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+            BFC_CK(c, cudaMemcpyAsync(gl.gseg, gsg.data(), (size_t)(S + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+            BFC_TRY(sync(c));   // the host vectors go out of scope
+        }
         launch_invert(perm[l], N, pos[l], c->stream);
         launch_gather_values(c->d_t, perm[l], N, c->tval[l], c->fp32, c->stream);
         BFC_LAUNCH_CHECK(c, "prep");
@@ -315,7 +355,7 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
     if (!isfinite(p.ridge_rel)) return fail(nullptr, BFC_EINVAL, "ridge_rel must be finite");
     if (p.prec != BFC_PREC_FP64 && p.prec != BFC_PREC_C64_FP64SOLVE)
         return fail(nullptr, BFC_EINVAL, "unknown precision");
-    if (p.gram_impl != 0 && p.gram_impl != 1) return fail(nullptr, BFC_EINVAL, "gram_impl must be 0 or 1");
+    if (p.gram_impl < 0 || p.gram_impl > 2) return fail(nullptr, BFC_EINVAL, "gram_impl must be 0, 1 or 2");
     if (p.max_sweeps < 0 || p.refine_sweeps < 0 || p.lr_sweeps < 0 || p.lr_rank < 0)
         return fail(nullptr, BFC_EINVAL, "sweep counts and lr_rank must be >= 0");
     if (p.init_kind < 0 || p.init_kind > 2) return fail(nullptr, BFC_EINVAL, "init_kind must be 0, 1 or 2");
@@ -337,7 +377,10 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
     c->fp32 = p.prec == BFC_PREC_C64_FP64SOLVE;
     c->vsz = c->fp32 ? 8 : 16;
     c->ridge = p.ridge_rel > 0.0 ? p.ridge_rel : (p.ridge_rel == 0.0 && c->fp32 ? 9.5367431640625e-07 : 0.0);
-    c->gram_tc = c->fp32 && p.gram_impl == 0 && p.r <= 8;
+    c->gram_tc = c->fp32 && p.gram_impl != 1 && p.r <= 8;
+    // grouped Gram (gram_impl 0) at the middle levels with few row / column
+    // groups per entry, below this ratio against the tensor-core kernel
+    c->grp_max_ratio = 0.45;
     bfc_status st = build(c, in);
     if (st != BFC_OK) {
         g_create_err = c->err;

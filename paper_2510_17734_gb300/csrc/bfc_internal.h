@@ -27,6 +27,17 @@ struct ProfPending {
 struct Ctx;
 bfc_status fail(Ctx* ctx, bfc_status st, const std::string& msg);
 
+// The entries of one middle level, inside every slice, in groups that share
+// one environment: one row (by_col = 0, they share h_m) or one column
+// (by_col = 1, they share w_m).  gstart[g] .. gstart[g+1] are the positions
+// of group g in the level order, gseg[k] the first group of slice k.
+struct GroupLevel {
+    int by_col = 0;
+    int64_t ngroups = 0;
+    int32_t* gstart = nullptr;
+    int32_t* gseg = nullptr;
+};
+
 // Device buffers of one completion problem.  Level l = 0 is the S^1 (row)
 // ordering of the training entries, l = 1..L the slice ordering of the middle
 // factor S^{l+1}, l = L+1 the S^{L+2} (column) ordering.
@@ -55,6 +66,8 @@ struct Ctx {
     std::vector<int32_t*> prv;   // l = 1..L : position in order l-1 (index 0 unused)
     int32_t* jL = nullptr;       // column index of the entries in order L
     std::vector<int32_t*> perm;  // L+2: entry index at each position of order l
+    std::vector<GroupLevel> grp; // L+2: row / column groups of the middle levels (empty otherwise)
+    double grp_max_ratio = 0.0;  // a middle level's Gram runs per group when groups / entries < this
 
     // environments (compute type): W[l] (l = 0..L) in order l, two H buffers
     void* W = nullptr;

@@ -2,6 +2,7 @@
 // Each function only enqueues work on the context stream.
 #pragma once
 
+#include "bfc_gram_grp.cuh"
 #include "bfc_gram_tc.cuh"
 #include "bfc_internal.h"
 #include "bfc_kernels.cuh"
@@ -15,6 +16,29 @@ template <typename T, int R> struct Path {
     typedef typename cvec<T>::type V;
     // the tensor-core Gram exists for the complex64 form with R * R <= 64
     static constexpr bool TC = sizeof(T) == 4 && R <= 8;
+    // the grouped Gram's 4 x 4 tiles need R in {4, 8}
+    static constexpr bool GRP = R == 4 || R == 8;
+
+    static cudaError_t set_grp_attr()
+    {
+        if constexpr (GRP)
+            return cudaFuncSetAttribute(k_mid_gram_grp<T, GRP ? R : 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)GrpCfg<T, GRP ? R : 4>::SMEM);
+        return cudaSuccess;
+    }
+
+    // Whether middle level m runs the grouped Gram (fewer groups than the
+    // context's ratio allows).
+    static bool grouped(const Ctx* c, int m)
+    {
+        if constexpr (!GRP) return false;
+        if ((int)c->grp.size() <= m) return false;
+        const GroupLevel& gl = c->grp[m];
+        // against the tensor-core kernel below 0.45 groups per entry, against
+        // the per-entry CUDA-core kernels below 0.9 (gram_impl 0 only)
+        const double ratio = c->P.gram_impl != 0 ? 0.0 : (c->gram_tc ? c->grp_max_ratio : 0.9);
+        return gl.ngroups > 0 && (double)gl.ngroups < ratio * (double)c->N;
+    }
 
     static cudaError_t set_tc_attr()
     {
@@ -35,6 +59,7 @@ template <typename T, int R> struct Path {
             e = cudaFuncSetAttribute(k_mid_fallback<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SolveCfg<T, R>::SMEM);
         if (e == cudaSuccess && TC) e = set_tc_attr();
+        if (e == cudaSuccess && GRP) e = set_grp_attr();
         if (e != cudaSuccess)
             return fail(c, BFC_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
         return BFC_OK;
@@ -118,10 +143,20 @@ template <typename T, int R> struct Path {
             V* hin = (m - 1) & 1 ? H1 : H0;
             V* hout = m & 1 ? H1 : H0;
             {
-                ProfScope ps(c, "mid_gram");
+                ProfScope ps(c, grouped(c, m) ? "mid_gram_grp" : "mid_gram");
                 bool done = false;
+                if constexpr (GRP) {
+                    if (grouped(c, m)) {
+                        const GroupLevel& gl = c->grp[m];
+                        constexpr int RG = GRP ? R : 4;
+                        k_mid_gram_grp<T, RG><<<(unsigned)S, GrpCfg<T, RG>::NTH, GrpCfg<T, RG>::SMEM, c->stream>>>(
+                            hin, W + (size_t)m * NR, (const V*)c->tval[m], gl.gseg, gl.gstart, gl.by_col, (V*)c->rec,
+                            (int)S);
+                        done = true;
+                    }
+                }
                 if constexpr (TC) {
-                    if (c->gram_tc) {
+                    if (!done && c->gram_tc) {
                         const unsigned g = (unsigned)(S < c->num_sms ? S : c->num_sms);
                         k_mid_gram_tc<TC ? R : 1><<<g, TcGram::NTH, TcGram::SMEM, c->stream>>>(
                             (const float2*)hin, (const float2*)(W + (size_t)m * NR), (const float2*)c->tval[m],

@@ -11,8 +11,14 @@ namespace bfc {
 
 // Level key of every entry: l = 0 row i, l = L+1 column j, otherwise the
 // slice id psi^{-1}(i_0..i_{L-m}, j_0..j_{m-1}) of S^{m+1}, m = l.
+// Sort key of every entry for one level: the row, the slice id of S^{level+1}
+// or the column.  With loc > 0 (middle levels) the key is composite,
+// slice * loc + (row or column index within the slice's block, i mod loc or
+// j mod loc), so that inside a slice the entries of one row (or column) are
+// contiguous.
 __global__ void k_level_keys(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj, int64_t N,
-                             int level, int L, int b, uint32_t* __restrict__ key, int32_t* __restrict__ idx)
+                             int level, int L, int b, int64_t loc, int by_col, uint32_t* __restrict__ key,
+                             int32_t* __restrict__ idx)
 {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N) return;
@@ -23,6 +29,7 @@ __global__ void k_level_keys(const int32_t* __restrict__ ii, const int32_t* __re
     else {
         const int m = level, pi = i / b, pj = j / b;
         k = (uint32_t)(((pi >> (m - 1)) << m) | (pj >> (L - m)));
+        if (loc > 0) k = (uint32_t)((int64_t)k * loc + (by_col ? j % loc : i % loc));
     }
     key[e] = k;
     idx[e] = (int32_t)e;
@@ -114,12 +121,14 @@ __global__ void __launch_bounds__(RS_TILE) k_rs_scatter(const uint32_t* __restri
 }
 
 // seg[k] = first position whose sorted key is >= k, seg[K] = N.
-__global__ void k_segments(const uint32_t* __restrict__ skeys, int64_t N, int64_t K, int32_t* __restrict__ seg)
+// Segment offsets of the sorted keys (key / div is the segment id, K segments).
+__global__ void k_segments(const uint32_t* __restrict__ skeys, int64_t N, int64_t K, int64_t div,
+                           int32_t* __restrict__ seg)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
-    const int64_t kp = skeys[p];
-    const int64_t kprev = p ? (int64_t)skeys[p - 1] : -1;
+    const int64_t kp = (int64_t)skeys[p] / div;
+    const int64_t kprev = p ? (int64_t)skeys[p - 1] / div : -1;
     for (int64_t k = kprev + 1; k <= kp; ++k) seg[k] = (int32_t)p;
     if (p == N - 1)
         for (int64_t k = kp + 1; k <= K; ++k) seg[k] = (int32_t)N;
@@ -324,11 +333,13 @@ __global__ void k_add_u64(unsigned long long* __restrict__ dst, const unsigned l
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 cudaError_t sort_level(const int32_t* d_i, const int32_t* d_j, int64_t N, int level, int L, int b,
-                       int64_t K, cudaStream_t st, SortScratch& s, int32_t* perm_out, int32_t* seg_out)
+                       int64_t K, int64_t loc, int by_col, cudaStream_t st, SortScratch& s, int32_t* perm_out,
+                       int32_t* seg_out, uint32_t** sorted_keys)
 {
-    k_level_keys<<<nblk(N, 256), 256, 0, st>>>(d_i, d_j, N, level, L, b, s.k0, s.v0);
+    k_level_keys<<<nblk(N, 256), 256, 0, st>>>(d_i, d_j, N, level, L, b, loc, by_col, s.k0, s.v0);
+    const int64_t KK = loc > 0 ? K * loc : K;
     int bits = 0;
-    while (((int64_t)1 << bits) < K) ++bits;
+    while (((int64_t)1 << bits) < KK) ++bits;
     const int passes = (bits + 7) / 8;
     const int64_t T = (N + RS_TILE - 1) / RS_TILE;
     uint32_t *ka = s.k0, *kb = s.k1;
@@ -341,8 +352,9 @@ cudaError_t sort_level(const int32_t* d_i, const int32_t* d_j, int64_t N, int le
         uint32_t* tk = ka; ka = kb; kb = tk;
         int32_t* tv = va; va = vb; vb = tv;
     }
-    k_segments<<<nblk(N, 256), 256, 0, st>>>(ka, N, K, seg_out);
+    k_segments<<<nblk(N, 256), 256, 0, st>>>(ka, N, K, loc > 0 ? loc : 1, seg_out);
     cudaMemcpyAsync(perm_out, va, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (sorted_keys) *sorted_keys = ka;
     return cudaGetLastError();
 }
 

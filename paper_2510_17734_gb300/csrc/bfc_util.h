@@ -18,8 +18,12 @@ struct SortScratch {
 // Stable sort of the entries by the key of `level` (K distinct key values):
 // perm_out[p] = entry at position p, seg_out[k] = first position of key k
 // (K + 1 values).
+// loc > 0 (middle levels): inside a slice, the entries are ordered by their
+// row (by_col = 0: i mod loc) or column (j mod loc) within the slice's block;
+// *sorted_keys (may be NULL) receives the device array of sorted keys (in s).
 cudaError_t sort_level(const int32_t* d_i, const int32_t* d_j, int64_t N, int level, int L, int b,
-                       int64_t K, cudaStream_t st, SortScratch& s, int32_t* perm_out, int32_t* seg_out);
+                       int64_t K, int64_t loc, int by_col, cudaStream_t st, SortScratch& s, int32_t* perm_out,
+                       int32_t* seg_out, uint32_t** sorted_keys);
 
 void launch_all_keys(const int32_t* ii, const int32_t* jj, int64_t M, int L, int b, int32_t* keys,
                      cudaStream_t st);

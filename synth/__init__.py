@@ -195,22 +195,24 @@ def config(index: int, n_override: int | None = None) -> Problem:
 RADON_SEED_BASE = 0xBFC20000
 
 
-def radon_problem(n: int = 1024, b: int = 4, r: int = 10, c_obs: float = 30.0, lam: float = 1e-8,
-                  sweeps: int = 20) -> Problem:
+def radon_problem(n: int = 4096, b: int = 4, r: int = 10, c_obs: float = 70.0, c_test: float = 10.0,
+                  lam: float = 1e-8, sweeps: int = 20) -> Problem:
     """The Radon-transform workload of Sec. 5.3: the matrix of radon_1d,
-    leaf size b (the paper's c = 4), rank r = 10, |Omega| = c_obs n log2 n
-    observed entries (30 n log2 n at n = 1024 in the paper's Fig. 8), drawn
-    uniformly without replacement; the last floor(0.1 |Omega|) draws are the
-    test set."""
+    leaf size b (the paper's c = 4), rank r, |Omega| = c_obs n log2 n
+    training and |Omega_test| = c_test n log2 n test entries, drawn uniformly
+    without replacement (the test entries are the last draws).  The default is
+    the paper's convergence study: n = 4096 (L = 10), 7 r n log2 n =
+    3,440,640 training and r n log2 n = 491,520 test entries with r = 10 (the
+    printed counts; the text's r = 12 is the estimate the completion used)."""
     L = int(round(math.log2(n // b)))
     if n != b << L:
         raise ValueError("n must equal b * 2^L")
-    n_obs = int(round(c_obs * n * math.log2(n)))
+    n_train = int(round(c_obs * n * math.log2(n)))
+    n_test = int(round(c_test * n * math.log2(n)))
+    n_obs = n_train + n_test
     seed = RADON_SEED_BASE + 16 * int(round(math.log2(n)))
     i, j = draw_pairs(n, n_obs, seed + SEED_OMEGA)
     vals = radon_1d(n, i, j)
-    n_test = int(math.floor(0.1 * n_obs))
-    n_train = n_obs - n_test
     return Problem(name=f"radon_n{n}", n=n, L=L, b=b, r=r, omega=0.0, h=0.0, lam=lam, sweeps=sweeps,
                    seed=seed, i=i[:n_train].copy(), j=j[:n_train].copy(), t=vals[:n_train].copy(),
                    it=i[n_train:].copy(), jt=j[n_train:].copy(), tt=vals[n_train:].copy(),

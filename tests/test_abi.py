@@ -61,6 +61,6 @@ def test_create_validates_sizes_before_touching_a_device(lib):
     with pytest.raises(bfc.BfcError, match="lambda"):
         bfc.bfc_create(prm, i, i, t)
     assert "lambda" in bfc.bfc_last_error(None)
-    prm = bfc.Params(n=64, L=2, b=16, r=2, lam=1e-6, prec=1, gram_impl=2)
+    prm = bfc.Params(n=64, L=2, b=16, r=2, lam=1e-6, prec=1, gram_impl=3)
     with pytest.raises(bfc.BfcError, match="gram_impl"):
         bfc.bfc_create(prm, i, i, t)

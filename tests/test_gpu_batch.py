@@ -59,7 +59,7 @@ def test_batch_autotuned_reaches_the_same_errors():
     for q, p in enumerate(probs):
         with make(p, PRECS[q], **kwargs(q, bfc.GRAM_CUDA)) as c:
             ref.append(c.complete()[-1]["train_rel_err"])
-    batch = [make(p, PRECS[q], **kwargs(q, bfc.GRAM_TENSOR)) for q, p in enumerate(probs)]
+    batch = [make(p, PRECS[q], **kwargs(q, bfc.GRAM_AUTO)) for q, p in enumerate(probs)]
     try:
         last = bfc.batch_complete(batch)
         for q in range(len(probs)):
