@@ -249,7 +249,7 @@ def group_counts(prob):
     return out
 
 
-def gram_rooflines(prob, prof, n_sweeps, c64, tc_levels, auto, peaks, fp32_meas, fp64_meas, args):
+def gram_rooflines(prob, prof, n_sweeps, c64, tc_levels, grouped, peaks, fp32_meas, fp64_meas, args):
     """Rooflines of the middle-level normal-equation kernels of the timed
     sweeps: the per-entry kernel (tensor cores, or CUDA cores) at the levels
     it ran, and the grouped CUDA-core kernel at the levels with few row /
@@ -258,9 +258,8 @@ def gram_rooflines(prob, prof, n_sweeps, c64, tc_levels, auto, peaks, fp32_meas,
     r, nnz = prob.r, prob.nnz
     D = r * r
     out = []
-    groups = group_counts(prob) if auto and r in (4, 8) else {}
-    ratio = 0.45 if tc_levels else 0.9
-    grouped = {m: g for m, g in groups.items() if g < ratio * nnz}
+    # grouped: {level: row / column groups} of the levels the library ran on
+    # the grouped Gram (bfc_level_groups)
     n_plain = prob.L - len(grouped)
     cnt, tot = prof.get("mid_gram", (0, 0.0))
     if cnt and n_plain:
@@ -302,13 +301,15 @@ def gram_rooflines(prob, prof, n_sweeps, c64, tc_levels, auto, peaks, fp32_meas,
                                        " FMA-chain peak (bfc_measure_alu_peaks, of measured)"})
     cnt, tot = prof.get("mid_gram_grp", (0, 0.0))
     if cnt and grouped:
-        ms = tot / cnt
+        # one profiling scope per grouped level covers its two kernels (group
+        # sums, then the per-slice Kronecker updates)
+        ms = tot / (n_sweeps * len(grouped))
         per_group = 8 * (D * (D + 1) // 2 + D)
         per_entry = 8 * (D + r)
         fl = (sum(grouped.values()) * per_group + len(grouped) * nnz * per_entry) / len(grouped)
         a = fl / (ms * 1e-3) / 1e12
         peak = fp32_meas if c64 else fp64_meas
-        out.append({"kernel": "k_mid_gram_grp", "bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s",
+        out.append({"kernel": "k_group_sums + k_mid_gram_grp", "bound": "alu", "achieved": a, "peak": peak, "unit": "TFLOP/s",
                     "frac": a / peak, "traffic": None, "launch_ms": ms, "launches_per_sweep": len(grouped),
                     "ms_per_sweep": tot / n_sweeps, "flop_per_launch": fl,
                     "groups_per_level": grouped,
@@ -320,11 +321,11 @@ def gram_rooflines(prob, prof, n_sweeps, c64, tc_levels, auto, peaks, fp32_meas,
     return out
 
 
-def lowrank_start(prob, bfc_mod, prec, gram=0):
+def lowrank_start(prob, bfc_mod, prec, gram=0, group_ratio=0.0):
     import synth
     A0, B0 = synth.random_lowrank_start(prob, prob.r)
     c = bfc_mod.Completion(prob.n, prob.L, prob.b, prob.r, prob.lam, prob.i, prob.j, prob.t,
-                           prob.it, prob.jt, prob.tt, prec=prec, gram_impl=gram)
+                           prob.it, prob.jt, prob.tt, prec=prec, gram_impl=gram, group_ratio=group_ratio)
     c.lowrank_init(A0, B0, 10)
     return c
 
@@ -732,7 +733,7 @@ def run_bfc(args, rank, world, local_rank):
     prec = bfc.PREC_C64 if args.prec == "c64" else bfc.PREC_FP64
 
     c = lowrank_start(prob, bfc, prec, gram={"auto": bfc.GRAM_AUTO, "tensor": bfc.GRAM_TENSOR,
-                                             "cuda": bfc.GRAM_CUDA}[args.gram])
+                                             "cuda": bfc.GRAM_CUDA}[args.gram], group_ratio=args.group_ratio)
     stream = torch.cuda.Stream(device=dev)
     bfc.bfc_set_stream(c.ctx, stream.cuda_stream)
 
@@ -826,7 +827,12 @@ def run_bfc(args, rank, world, local_rank):
     fp32_meas, fp64_meas = bfc.bfc_measure_alu_peaks()
     n_sweeps = max(args.steps, 1)
     tc_levels = prec == bfc.PREC_C64 and args.gram != "cuda" and prob.r <= 8
-    entries = gram_rooflines(prob, prof, n_sweeps, prec == bfc.PREC_C64, tc_levels, args.gram == "auto",
+    grouped = {}
+    for m in range(1, prob.L + 1):
+        ng, on = c.level_groups(m)
+        if on:
+            grouped[m] = ng
+    entries = gram_rooflines(prob, prof, n_sweeps, prec == bfc.PREC_C64, tc_levels, grouped,
                              peaks, fp32_meas, fp64_meas, args)
     entries += kernel_rooflines(prob, prof, stats, peaks, fp32_meas) if prec == bfc.PREC_C64 else []
     if not entries:
@@ -838,6 +844,7 @@ def run_bfc(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "c64+f64" if prec == bfc.PREC_C64 else "f64",
             "data": "synthetic",
             "config": {"workload": workload, "precision": args.prec, "gram": args.gram,
+                       "grouped_levels": sorted(grouped),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "working set > L2 (no flush)", "nnz_train": prob.nnz},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * P,
@@ -910,6 +917,8 @@ def main():
     ap.add_argument("--no-radon", action="store_true", help="skip the Radon-transform run")
     ap.add_argument("--learned-train", type=int, default=64, help="training completions of the learned start")
     ap.add_argument("--learned-epochs", type=int, default=2500, help="training epochs of the learned start")
+    ap.add_argument("--group-ratio", type=float, default=0.0,
+                    help="groups-per-entry threshold of the grouped Gram (0: library default, < 0: never)")
     ap.add_argument("--gram", default="auto", choices=["auto", "tensor", "cuda"],
                     help="middle-level Gram: auto (grouped CUDA-core kernel at levels with few row / column "
                          "groups, tcgen05 per entry elsewhere), tensor (tcgen05 per entry), cuda (CUDA cores "

@@ -103,13 +103,30 @@ typedef struct {
                                0 selects the default (2^-20, the complex64
                                rounding level of the normal equations, in the
                                precision form; none in FP64); < 0 disables  */
-    int32_t gram_impl;      /* precision form, per-slice normal equations of
-                               the middle levels: 0 = tensor cores (tcgen05,
-                               three-term TF32 products, Kahan-folded every
-                               32 entries) for r <= 8 and CUDA cores for
-                               r > 8; 1 = CUDA cores (complex64 FMA) always */
+    int32_t gram_impl;      /* per-slice normal equations of the middle
+                               levels.  0 = automatic: for r = 4 or 8, a
+                               level whose row (or column) groups are few
+                               against its entries (below group_ratio of
+                               them) runs the grouped Gram (the entries of one row
+                               / column of a slice share an environment, so
+                               the sums are taken per group and the Gram is
+                               the sum of Kronecker products of the group
+                               sums; both precisions); the other levels run
+                               the per-entry kernel of 2 (precision form,
+                               r <= 8) or of 1.  1 = per-entry CUDA cores
+                               (complex64 FMA, or FP64) at every level.  2 =
+                               per-entry tensor cores (tcgen05, three-term
+                               TF32 products, Kahan-folded every 32 entries)
+                               at every level in the precision form for
+                               r <= 8, CUDA cores otherwise.  Any other
+                               value is BFC_EINVAL.                         */
     int32_t lr2bf_oversample; /* oversampling p of Alg. 2 for init_kind 2
                                (0 selects 5); r + p <= 32                   */
+    double group_ratio;     /* gram_impl 0: groups-per-entry threshold of the
+                               grouped Gram.  0 selects the default (0.2
+                               next to the tensor-core kernel, 0.9 next to
+                               the CUDA-core one); < 0 never groups; > 0
+                               is used as given                             */
 } bfc_params;
 
 typedef struct {
@@ -123,8 +140,10 @@ typedef struct {
     int64_t refined_fallbacks; /* precision form: FP64 Cholesky fallbacks    */
     int64_t refine_steps;   /* precision form: refinement steps taken        */
     int64_t launches;       /* kernels this call launched (sweep + errors)   */
-    int32_t gram_impl;      /* middle-level Gram kernel used: 0 tensor cores,
-                               1 CUDA cores, -1 FP64 path                    */
+    int32_t gram_impl;      /* per-entry middle-level Gram kernel of the
+                               precision form (levels not on the grouped
+                               Gram): 0 tensor cores, 1 CUDA cores; -1 FP64
+                               path                                         */
 } bfc_sweep_stats;
 
 typedef struct {
@@ -293,8 +312,8 @@ bfc_status bfc_complete(bfc_ctx* ctx, bfc_sweep_stats* history, int32_t history_
  * one graph whose child graphs are the sweeps of all unfinished problems
  * (rebuilt only when that set changes), so the problems run concurrently
  * on the GPU from a single launch per round.  In the precision form with
- * gram_impl 0, the Gram kernel is autotuned per rank: the first problem of
- * each rank r <= 8 runs one warm-up and one timed sweep with each kernel
+ * gram_impl 0, the per-entry Gram kernel is autotuned per rank: the first
+ * problem of each rank r <= 8 runs one warm-up and one timed sweep with each kernel
  * (ordinary sweeps, counted) and the faster serves all problems of that
  * rank.  last (may be NULL) receives the last sweep's statistics of each
  * problem.  A context may appear once; contexts must live on the current
@@ -395,6 +414,17 @@ bfc_status bfc_decode(int64_t n, int32_t L, int32_t b, int64_t m, const int32_t*
  * a key; seg[k] .. seg[k+1] is the range of key k (n + 1 values for levels 0
  * and L+1, 2^{L+1} + 1 otherwise).  Host arrays; either may be NULL. */
 bfc_status bfc_get_order(bfc_ctx* ctx, int32_t level, int32_t* perm, int32_t* seg);
+
+/* Row / column groups of one middle level (1..L): inside every slice of
+ * S^{level+1}, the entries of one row (levels with 2 level <= L + 1) or of
+ * one column share the environment on that side; *ngroups receives the
+ * number of such groups over all slices (0 where groups are not formed: the
+ * outer levels 0 and L+1, or a level whose composite sort key would not fit
+ * 32 bits), *grouped whether this context's sweeps run the level's normal
+ * equations per group (gram_impl, group_ratio).  Either pointer may be NULL;
+ * EINVAL on a level outside [0, L+1].  No counterpart in the paper: the
+ * grouping is an implementation of the slice sums of Alg. 1. */
+bfc_status bfc_level_groups(bfc_ctx* ctx, int32_t level, int64_t* ngroups, int32_t* grouped);
 
 /* Per-kernel device-time accounting with CUDA events on the context stream
  * (off by default).  Enabling resets the counters. */

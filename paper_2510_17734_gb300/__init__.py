@@ -30,7 +30,7 @@ __all__ = [
     "bfc_mlp_create", "bfc_mlp_dims", "bfc_mlp_num_params", "bfc_mlp_get_params", "bfc_mlp_set_params",
     "bfc_mlp_set_scaling", "bfc_mlp_forward", "bfc_mlp_grad", "bfc_mlp_train", "bfc_mlp_destroy",
     "bfc_init_learned", "bfc_canonicalize", "Mlp", "bfc_measure_alu_peaks", "bfc_inject_fault",
-    "bfc_adam", "bfc_adf", "bfc_matvec", "bfc_lowrank_to_butterfly",
+    "bfc_adam", "bfc_adf", "bfc_matvec", "bfc_lowrank_to_butterfly", "bfc_level_groups",
 ]
 
 PREC_FP64 = 0
@@ -49,7 +49,7 @@ exported_symbols = (
     "bfc_mlp_create", "bfc_mlp_dims", "bfc_mlp_num_params", "bfc_mlp_get_params", "bfc_mlp_set_params",
     "bfc_mlp_set_scaling", "bfc_mlp_forward", "bfc_mlp_grad", "bfc_mlp_train", "bfc_mlp_destroy",
     "bfc_init_learned", "bfc_canonicalize", "bfc_measure_alu_peaks", "bfc_inject_fault",
-    "bfc_adam", "bfc_adf", "bfc_matvec", "bfc_lowrank_to_butterfly",
+    "bfc_adam", "bfc_adf", "bfc_matvec", "bfc_lowrank_to_butterfly", "bfc_level_groups",
     "bfc_profile_enable", "bfc_profile_read", "bfc_last_error", "bfc_destroy",
 )
 
@@ -67,7 +67,8 @@ class Params(ctypes.Structure):
                 ("init_kind", ctypes.c_int32), ("lr_rank", ctypes.c_int32),
                 ("lr_sweeps", ctypes.c_int32), ("values_on_device", ctypes.c_int32),
                 ("refine_sweeps", ctypes.c_int32), ("ridge_rel", ctypes.c_double),
-                ("gram_impl", ctypes.c_int32), ("lr2bf_oversample", ctypes.c_int32)]
+                ("gram_impl", ctypes.c_int32), ("lr2bf_oversample", ctypes.c_int32),
+                ("group_ratio", ctypes.c_double)]
 
 
 class SweepStats(ctypes.Structure):
@@ -164,6 +165,8 @@ def load():
         lib.bfc_decode.restype = i32
         lib.bfc_get_order.argtypes = [vp, i32, vp, vp]
         lib.bfc_get_order.restype = i32
+        lib.bfc_level_groups.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(i32)]
+        lib.bfc_level_groups.restype = i32
         lib.bfc_residual_noalloc.argtypes = [i64, i32, i32, i32, vp, i64, vp, vp, vp, vp, vp]
         lib.bfc_residual_noalloc.restype = i32
         lib.bfc_adam.argtypes = [vp, i32, dbl, dbl, dbl, dbl, sp, i32, ctypes.POINTER(i32)]
@@ -439,6 +442,13 @@ def bfc_get_order(ctx, level: int, N: int, K: int):
     return perm, seg
 
 
+def bfc_level_groups(ctx, level: int):
+    ng = ctypes.c_int64(0)
+    gr = ctypes.c_int32(0)
+    _check(load().bfc_level_groups(ctx, level, ctypes.byref(ng), ctypes.byref(gr)), ctx)
+    return int(ng.value), bool(gr.value)
+
+
 def _check_cuda_tensor(x, what, dtype_name, numel=None, min_numel=None):
     if not hasattr(x, "is_cuda") or not x.is_cuda:
         raise BfcError(1, f"{what} must be a CUDA tensor")
@@ -504,12 +514,13 @@ class Completion:
 
     def __init__(self, n, L, b, r, lam, i, j, t, it=None, jt=None, tt=None, prec=PREC_FP64,
                  max_sweeps=20, tol=1e-3, seed=0, init_kind=0, lr_rank=0, lr_sweeps=10,
-                 refine_sweeps=0, ridge_rel=0.0, gram_impl=GRAM_AUTO, lr2bf_oversample=0):
+                 refine_sweeps=0, ridge_rel=0.0, gram_impl=GRAM_AUTO, lr2bf_oversample=0, group_ratio=0.0):
         self.n, self.L, self.b, self.r = int(n), int(L), int(b), int(r)
         self.params = Params(n=n, L=L, b=b, r=r, lam=lam, prec=prec, max_sweeps=max_sweeps, tol=tol,
                              seed=seed, init_kind=init_kind, lr_rank=lr_rank, lr_sweeps=lr_sweeps,
                              values_on_device=0, refine_sweeps=refine_sweeps, ridge_rel=ridge_rel,
-                             gram_impl=gram_impl, lr2bf_oversample=lr2bf_oversample)
+                             gram_impl=gram_impl, lr2bf_oversample=lr2bf_oversample,
+                             group_ratio=group_ratio)
         self.P = bfc_num_params(n, L, b, r)
         self._nnz = len(i)
         self.ctx = bfc_create(self.params, i, j, t, it, jt, tt)
@@ -566,6 +577,10 @@ class Completion:
         N = int(self._nnz)
         K = self.n if level in (0, self.L + 1) else (1 << (self.L + 1))
         return bfc_get_order(self.ctx, level, N, K)
+
+    def level_groups(self, level):
+        """(groups, grouped) of a middle level (bfc_level_groups)."""
+        return bfc_level_groups(self.ctx, level)
 
     def canonicalize(self):
         bfc_canonicalize(self.ctx)

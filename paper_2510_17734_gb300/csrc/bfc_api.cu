@@ -269,20 +269,31 @@ static bfc_status build(Ctx* c, const Inputs& in)
             for (int64_t p = 0; p < N; ++p)
                 if (p == 0 || hkeys[p] != hkeys[p - 1]) gst.push_back((int32_t)p);
             const int64_t G = (int64_t)gst.size();
-            gst.push_back((int32_t)N);
-            int64_t g = 0;
-            for (int64_t k = 0; k <= S; ++k) {
-                while (g < G && (int64_t)(hkeys[gst[g]] / (uint64_t)loc) < k) ++g;
-                gsg[k] = (int32_t)g;
-            }
             GroupLevel& gl = c->grp[l];
             gl.by_col = by_col;
             gl.ngroups = G;
-            BFC_TRY(dalloc(c, (void**)&gl.gstart, (size_t)(G + 1) * 4, "group offsets"));
-            BFC_TRY(dalloc(c, (void**)&gl.gseg, (size_t)(S + 1) * 4, "slice group offsets"));
-            BFC_CK(c, cudaMemcpyAsync(gl.gstart, gst.data(), (size_t)(G + 1) * 4, cudaMemcpyHostToDevice, c->stream));
-            BFC_CK(c, cudaMemcpyAsync(gl.gseg, gsg.data(), (size_t)(S + 1) * 4, cudaMemcpyHostToDevice, c->stream));
-            BFC_TRY(sync(c));   // the host vectors go out of scope
+            const double ratio = c->gram_tc ? c->grp_max_ratio : c->grp_cuda_ratio;
+            if ((c->r == 4 || c->r == 8) && c->P.gram_impl == 0 && (double)G < ratio * (double)N) {
+                gst.push_back((int32_t)N);
+                int64_t g = 0;
+                for (int64_t k = 0; k <= S; ++k) {
+                    while (g < G && (int64_t)(hkeys[gst[g]] / (uint64_t)loc) < k) ++g;
+                    gsg[k] = (int32_t)g;
+                }
+                BFC_TRY(dalloc(c, (void**)&gl.gstart, (size_t)(G + 1) * 4, "group offsets"));
+                BFC_TRY(dalloc(c, (void**)&gl.gseg, (size_t)(S + 1) * 4, "slice group offsets"));
+                BFC_CK(c, cudaMemcpyAsync(gl.gstart, gst.data(), (size_t)(G + 1) * 4, cudaMemcpyHostToDevice,
+                                          c->stream));
+                BFC_CK(c, cudaMemcpyAsync(gl.gseg, gsg.data(), (size_t)(S + 1) * 4, cudaMemcpyHostToDevice,
+                                          c->stream));
+                BFC_TRY(sync(c));   // the host vectors go out of scope
+            } else {
+                // the level runs a per-entry Gram: its slices keep the entries
+                // in input order (a row- or column-sorted slice makes the
+                // per-entry partial sums coherent, and their rounding larger)
+                BFC_CK(c, sort_level(c->d_i, c->d_j, N, l, L, c->b, K, 0, 0, c->stream, ss, perm[l], c->seg[l],
+                                     nullptr));
+            }
         }
         launch_invert(perm[l], N, pos[l], c->stream);
         launch_gather_values(c->d_t, perm[l], N, c->tval[l], c->fp32, c->stream);
@@ -335,6 +346,14 @@ static bfc_status build(Ctx* c, const Inputs& in)
     }
     const Ops* ops = get_ops(c->fp32, r);
     BFC_TRY(dalloc(c, &c->rec, ops->record_bytes(n, S), "normal-equation records"));
+    // group records [s | M | v] of the grouped Gram (ranks 4 and 8): sized for
+    // the largest level whose order was grouped
+    if ((r == 4 || r == 8) && c->P.gram_impl == 0) {
+        int64_t gmax = 0;
+        for (const GroupLevel& gl : c->grp)
+            if (gl.gstart) gmax = std::max(gmax, gl.ngroups);
+        if (gmax > 0) BFC_TRY(dalloc(c, &c->grec, (size_t)gmax * (2 * r + r * r) * c->vsz, "group records"));
+    }
     const size_t fbb = ops->fallback_bytes(S);
     if (fbb > 0 && L > 0) {
         BFC_TRY(dalloc(c, (void**)&c->fb, fbb, "FP64 fallback records"));
@@ -356,6 +375,7 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
     if (p.prec != BFC_PREC_FP64 && p.prec != BFC_PREC_C64_FP64SOLVE)
         return fail(nullptr, BFC_EINVAL, "unknown precision");
     if (p.gram_impl < 0 || p.gram_impl > 2) return fail(nullptr, BFC_EINVAL, "gram_impl must be 0, 1 or 2");
+    if (!(p.group_ratio == p.group_ratio)) return fail(nullptr, BFC_EINVAL, "group_ratio is NaN");
     if (p.max_sweeps < 0 || p.refine_sweeps < 0 || p.lr_sweeps < 0 || p.lr_rank < 0)
         return fail(nullptr, BFC_EINVAL, "sweep counts and lr_rank must be >= 0");
     if (p.init_kind < 0 || p.init_kind > 2) return fail(nullptr, BFC_EINVAL, "init_kind must be 0, 1 or 2");
@@ -379,8 +399,12 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
     c->ridge = p.ridge_rel > 0.0 ? p.ridge_rel : (p.ridge_rel == 0.0 && c->fp32 ? 9.5367431640625e-07 : 0.0);
     c->gram_tc = c->fp32 && p.gram_impl != 1 && p.r <= 8;
     // grouped Gram (gram_impl 0) at the middle levels with few row / column
-    // groups per entry, below this ratio against the tensor-core kernel
-    c->grp_max_ratio = 0.45;
+    // groups per entry: below this ratio against the tensor-core kernel (a
+    // group's compensated Kronecker update and its sums cost about what four
+    // to five entries cost there), below 0.9 against the per-entry CUDA-core
+    // kernel
+    c->grp_max_ratio = p.group_ratio > 0.0 ? p.group_ratio : (p.group_ratio < 0.0 ? 0.0 : 0.2);
+    c->grp_cuda_ratio = p.group_ratio > 0.0 ? p.group_ratio : (p.group_ratio < 0.0 ? 0.0 : 0.9);
     bfc_status st = build(c, in);
     if (st != BFC_OK) {
         g_create_err = c->err;
@@ -719,6 +743,16 @@ static bfc_status lbfgs_impl(Ctx* c, int iters, int m, bfc_sweep_stats* history,
     release();
     if (st == BFC_OK) st = sync(c);
     return st;
+}
+
+bool level_grouped(const Ctx* c, int m)
+{
+    if (c->P.gram_impl != 0 || (c->r != 4 && c->r != 8) || !c->grec) return false;
+    if (m < 1 || m > c->L || (int)c->grp.size() <= m) return false;
+    const GroupLevel& gl = c->grp[m];
+    if (!gl.gstart) return false;   // level order not grouped at build time
+    const double ratio = c->gram_tc ? c->grp_max_ratio : c->grp_cuda_ratio;
+    return gl.ngroups > 0 && (double)gl.ngroups < ratio * (double)c->N;
 }
 
 }  // namespace bfc
@@ -1405,6 +1439,17 @@ bfc_status bfc_decode(int64_t n, int32_t L, int32_t b, int64_t m, const int32_t*
     cudaFree(dj);
     cudaFree(dk);
     if (e != cudaSuccess) return fail(nullptr, BFC_ECUDA, std::string("decode: ") + cudaGetErrorString(e));
+    return BFC_OK;
+}
+
+bfc_status bfc_level_groups(bfc_ctx* ctx, int32_t level, int64_t* ngroups, int32_t* grouped)
+{
+    Ctx* c = (Ctx*)ctx;
+    if (!c) return BFC_EINVAL;
+    if (level < 0 || level > c->L + 1) return fail(c, BFC_EINVAL, "level outside [0, L+1]");
+    const bool mid = level >= 1 && level <= c->L && (int)c->grp.size() > level;
+    if (ngroups) *ngroups = mid ? c->grp[level].ngroups : 0;
+    if (grouped) *grouped = level_grouped(c, level) ? 1 : 0;
     return BFC_OK;
 }
 

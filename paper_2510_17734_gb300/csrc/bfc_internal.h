@@ -67,7 +67,10 @@ struct Ctx {
     int32_t* jL = nullptr;       // column index of the entries in order L
     std::vector<int32_t*> perm;  // L+2: entry index at each position of order l
     std::vector<GroupLevel> grp; // L+2: row / column groups of the middle levels (empty otherwise)
+    void* grec = nullptr;        // group records [s | M | v] of the level being solved (grouped Gram)
     double grp_max_ratio = 0.0;  // a middle level's Gram runs per group when groups / entries < this
+                                 // (next to the tensor-core kernel)
+    double grp_cuda_ratio = 0.0; // the same next to the per-entry CUDA-core kernel
 
     // environments (compute type): W[l] (l = 0..L) in order l, two H buffers
     void* W = nullptr;
@@ -124,6 +127,10 @@ struct Ctx {
 bfc_status dalloc(Ctx* c, void** p, size_t bytes, const char* what);
 bfc_status ensure_tmp(Ctx* c, size_t bytes);
 
+// Whether middle level m runs the grouped Gram: gram_impl 0, r = 4 or 8,
+// and fewer groups than the threshold against the per-entry kernel in use.
+bool level_grouped(const Ctx* c, int m);
+
 // Profiling scope around one launch.
 struct ProfScope {
     Ctx* c;
@@ -134,6 +141,12 @@ struct ProfScope {
     // whether or not profiling is on).
     ProfScope(Ctx* ctx, const char* name, int kernels = 1);
     ~ProfScope();
+    // the scope launched k more kernels than it was opened with
+    void add_kernels(int k)
+    {
+        kernels += k;
+        c->n_launch += k;
+    }
 };
 void prof_collect(Ctx* c);
 

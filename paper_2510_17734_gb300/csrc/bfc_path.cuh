@@ -21,9 +21,14 @@ template <typename T, int R> struct Path {
 
     static cudaError_t set_grp_attr()
     {
-        if constexpr (GRP)
-            return cudaFuncSetAttribute(k_mid_gram_grp<T, GRP ? R : 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if constexpr (GRP) {
+            cudaError_t e = cudaFuncSetAttribute(k_mid_gram_grp<T, GRP ? R : 4, 0>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)GrpCfg<T, GRP ? R : 4>::SMEM);
+            if (e != cudaSuccess) return e;
+            return cudaFuncSetAttribute(k_mid_gram_grp<T, GRP ? R : 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)GrpCfg<T, GRP ? R : 4>::SMEM);
+        }
         return cudaSuccess;
     }
 
@@ -32,12 +37,7 @@ template <typename T, int R> struct Path {
     static bool grouped(const Ctx* c, int m)
     {
         if constexpr (!GRP) return false;
-        if ((int)c->grp.size() <= m) return false;
-        const GroupLevel& gl = c->grp[m];
-        // against the tensor-core kernel below 0.45 groups per entry, against
-        // the per-entry CUDA-core kernels below 0.9 (gram_impl 0 only)
-        const double ratio = c->P.gram_impl != 0 ? 0.0 : (c->gram_tc ? c->grp_max_ratio : 0.9);
-        return gl.ngroups > 0 && (double)gl.ngroups < ratio * (double)c->N;
+        return level_grouped(c, m);
     }
 
     static cudaError_t set_tc_attr()
@@ -149,9 +149,17 @@ template <typename T, int R> struct Path {
                     if (grouped(c, m)) {
                         const GroupLevel& gl = c->grp[m];
                         constexpr int RG = GRP ? R : 4;
-                        k_mid_gram_grp<T, RG><<<(unsigned)S, GrpCfg<T, RG>::NTH, GrpCfg<T, RG>::SMEM, c->stream>>>(
-                            hin, W + (size_t)m * NR, (const V*)c->tval[m], gl.gseg, gl.gstart, gl.by_col, (V*)c->rec,
-                            (int)S);
+                        typedef GsumCfg<T, RG> GS;
+                        k_group_sums<T, RG><<<nblocks(gl.ngroups, GS::GB), GS::NTH, GS::SMEM, c->stream>>>(
+                            hin, W + (size_t)m * NR, (const V*)c->tval[m], gl.gstart, (int)gl.ngroups, gl.by_col,
+                            (V*)c->grec);
+                        if (gl.by_col)
+                            k_mid_gram_grp<T, RG, 1><<<(unsigned)S, GrpCfg<T, RG>::NTH, GrpCfg<T, RG>::SMEM,
+                                                       c->stream>>>((const V*)c->grec, gl.gseg, (V*)c->rec, (int)S);
+                        else
+                            k_mid_gram_grp<T, RG, 0><<<(unsigned)S, GrpCfg<T, RG>::NTH, GrpCfg<T, RG>::SMEM,
+                                                       c->stream>>>((const V*)c->grec, gl.gseg, (V*)c->rec, (int)S);
+                        ps.add_kernels(1);
                         done = true;
                     }
                 }

@@ -7,13 +7,15 @@ workload below it computes the low-rank start (Alg. 1 with L = 0, rank r,
 after every sweep, the training error and test error of Eq.
 (BF_convergence) and the regularized objective.
 
-    python tests/golden/make_oracle_sweeps.py [cfg3|rule16k|all] [threads]
+    python tests/golden/make_oracle_sweeps.py [cfg3|rule16k|rule16k_ridge|all] [threads]
 
 Workloads:
   cfg3     n = 65536, L = 12, b = 16, r = 8, omega = pi n / 16, h = 1.5,
            |Omega| = 4 n log2 n, lambda = 1e-7 (synth.config(3)), 8 sweeps
   rule16k  the same operator family at n = 16384 (L = 10) with the paper's
            sampling rule |Omega| = 6 r n log2 n (Sec. 5.1), 10 sweeps
+  rule16k_ridge  rule16k with every system solved under the ridge floor
+           max(lambda, 2^-20 tr(K) / dim) (the precision form's reading)
 """
 import math
 import os
@@ -33,12 +35,17 @@ def rule16k_problem():
                               6 * r * n * int(round(math.log2(n))), 1e-7, 10, synth.SEED_BASE + 16 * 3)
 
 
+RULE16K = ("n=16384 L=10 b=16 r=8 omega=pi*n/16 h=1.5 |Omega|=48 n log2 n (6 r n log2 n, Sec. 5.1) "
+           "lambda=1e-7 seed=synth.SEED_BASE+48")
+
+# name: (problem, sweeps, description, ridge floor of every system's solve)
 WORKLOADS = {
     "cfg3": (lambda: synth.config(3), 8,
-             "n=65536 L=12 b=16 r=8 omega=pi*n/16 h=1.5 |Omega|=4 n log2 n lambda=1e-7 (synth.config(3))"),
-    "rule16k": (rule16k_problem, 10,
-                "n=16384 L=10 b=16 r=8 omega=pi*n/16 h=1.5 |Omega|=48 n log2 n (6 r n log2 n, Sec. 5.1) "
-                "lambda=1e-7 seed=synth.SEED_BASE+48"),
+             "n=65536 L=12 b=16 r=8 omega=pi*n/16 h=1.5 |Omega|=4 n log2 n lambda=1e-7 (synth.config(3))", 0.0),
+    "rule16k": (rule16k_problem, 10, RULE16K, 0.0),
+    # the same sweeps under the complex64 precision form's reading of the
+    # regularization: every system solved with max(lambda, 2^-20 tr(K) / dim)
+    "rule16k_ridge": (rule16k_problem, 10, RULE16K + " ridge_rel=2^-20", 2.0 ** -20),
 }
 
 
@@ -51,7 +58,7 @@ def oracle_start(p):
 
 
 def run(name, threads):
-    make, sweeps, desc = WORKLOADS[name]
+    make, sweeps, desc, ridge = WORKLOADS[name]
     p = make()
     out = os.path.join(HERE, f"oracle_sweeps_{name}.txt")
     with oracle.threads(threads):
@@ -62,7 +69,7 @@ def run(name, threads):
                  oracle.objective(p.n, p.L, p.b, p.r, p.lam, X, p.i, p.j, p.t))]
         print(f"{name}: start {rows[-1]} ({time.time() - t0:.0f} s)", flush=True)
         for s in range(1, sweeps + 1):
-            X, st = oracle.als_sweep(p.n, p.L, p.b, p.r, p.lam, X, p.i, p.j, p.t)
+            X, st = oracle.als_sweep(p.n, p.L, p.b, p.r, p.lam, X, p.i, p.j, p.t, ridge_rel=ridge)
             te = oracle.rel_err(p.n, p.L, p.b, p.r, X, p.it, p.jt, p.tt)
             rows.append((s, st["train_rel_err"], te, st["objective"]))
             print(f"{name}: sweep {s} {rows[-1]} ({time.time() - t0:.0f} s)", flush=True)

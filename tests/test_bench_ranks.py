@@ -57,10 +57,10 @@ def test_kernel_rooflines_arithmetic():
     p = synth.config(3)                     # n = 65536, L = 12, r = 8
     nnz, S = p.nnz, 1 << (p.L + 1)
     groups = bench.group_counts(p)
-    grouped = {m: g for m, g in groups.items() if g < 0.45 * nnz}
+    grouped = {m: g for m, g in groups.items() if g < 0.2 * nnz}
     nplain = p.L - len(grouped)
     prof = {"env_right": (24, 24 * 0.1), "mid_gram": (2 * nplain, 2 * nplain * 1.0),
-            "mid_gram_grp": (2 * len(grouped), 2 * len(grouped) * 0.5), "mid_solve": (24, 24 * 0.5),
+            "mid_gram_grp": (4 * len(grouped), 2 * len(grouped) * 0.5), "mid_solve": (24, 24 * 0.5),
             "eval": (2, 2 * 0.25)}
     stats = [{"refine_steps": p.L * S}, {"refine_steps": p.L * S}]
     rows = {r["kernel"]: r for r in bench.kernel_rooflines(p, prof, stats, {"hbm_gbs": 6000.0}, 80.0)}
@@ -70,15 +70,15 @@ def test_kernel_rooflines_arithmetic():
     assert env["frac"] == pytest.approx(env["achieved"] / 6000.0)
     assert env["ms_per_sweep"] == pytest.approx(1.2)
     args = type("A", (), {"n": 0})()
-    gram = {r["kernel"]: r for r in bench.gram_rooflines(p, prof, 2, True, True, True, {"bf16_tflops_sustained": 1700.0},
-                                                           80.0, 1.2, args)}
+    gram = {r["kernel"]: r for r in bench.gram_rooflines(p, prof, 2, True, True, grouped,
+                                                           {"bf16_tflops_sustained": 1700.0}, 80.0, 1.2, args)}
     # rows (2 m <= L + 1) or columns: level 1 has 16 rows per slice block
     assert groups[1] <= (1 << (p.L + 1)) * 16 and groups[p.L] <= (1 << (p.L + 1)) * 16
     tc = gram["k_mid_gram_tc"]
     assert tc["flop_per_launch"] == nnz * 8 * (64 * 65 // 2 + 64)
     assert tc["fp32_frac"] == pytest.approx(tc["flop_per_launch"] / 1e-3 / 1e12 / 80.0)
     assert tc["peak"] == pytest.approx(1700.0 * 1.1 / 2.25)
-    grp = gram["k_mid_gram_grp"]
+    grp = gram["k_group_sums + k_mid_gram_grp"]
     fl = (sum(grouped.values()) * 8 * (64 * 65 // 2 + 64) + len(grouped) * nnz * 8 * (64 + 8)) / len(grouped)
     assert grp["flop_per_launch"] == pytest.approx(fl)
     assert grp["frac"] == pytest.approx(fl / 0.5e-3 / 1e12 / 80.0)

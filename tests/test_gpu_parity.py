@@ -84,20 +84,39 @@ def test_decode_bit_exact_large_sample():
         assert list(keys[e]) == want
 
 
-def test_orders_are_stable_sorts(cfg1):
+@pytest.mark.parametrize("group_ratio", [0.0, 2.0, -1.0])
+def test_orders_are_stable_sorts(cfg1, group_ratio):
+    """Level orders: stable sorts of the entries by row, by the oracle's slice
+    id of S^{m+1} and by column; inside a slice of a middle level that runs
+    the grouped Gram the entries are further ordered by their row (levels
+    with 2m <= L + 1) or column (the groups that share an environment),
+    stably; the other middle levels keep input order inside a slice."""
     p, X0 = cfg1
-    with make(p, bfc.PREC_C64) as c:
+    with make(p, bfc.PREC_C64, group_ratio=group_ratio) as c:
+        n_grouped = 0
         for level in range(p.L + 2):
+            sub = np.zeros(p.nnz, dtype=np.int64)
             if level == 0:
                 key = p.i.astype(np.int64)
             elif level == p.L + 1:
                 key = p.j.astype(np.int64)
             else:
                 key = np.array([oracle.slice_id(a, b_, level, p.L, p.b) for a, b_ in zip(p.i, p.j)])
+                other = (p.j if 2 * level > p.L + 1 else p.i).astype(np.int64)
+                ngroups, grouped = c.level_groups(level)
+                # groups: distinct (slice, row) or (slice, column) pairs
+                assert ngroups == np.unique(key * p.n + other).size
+                if grouped:
+                    sub = other
+                    n_grouped += 1
             perm, seg = c.order(level)
-            np.testing.assert_array_equal(perm, np.argsort(key, kind="stable"))
+            np.testing.assert_array_equal(perm, np.lexsort((sub, key)))   # stable, key then sub
             K = p.n if level in (0, p.L + 1) else 1 << (p.L + 1)
             np.testing.assert_array_equal(seg, np.searchsorted(np.sort(key), np.arange(K + 1)))
+        if group_ratio == 2.0:
+            assert n_grouped == p.L
+        elif group_ratio < 0:
+            assert n_grouped == 0
 
 
 # ------------------------------------------------------------------ eval
@@ -123,7 +142,9 @@ def test_one_sweep_parity(request, which, prec):
     Xo, st_o = oracle_sweep(p, X0, prec)
     with make(p, prec) as c:
         c.set_factors(X0)
+        c.profile(True)
         st = c.sweep()
+        prof = c.profile_read()
         Xg = c.get_factors()
     tol = TOL[prec]
     assert abs(st["objective"] - st_o["objective"]) <= tol * abs(st_o["objective"])
@@ -148,9 +169,11 @@ def test_one_sweep_parity(request, which, prec):
         assert rel_dev(xg, xp) <= rel_dev(xo, xp) + tol
     # kernels per sweep: 1 + L right environments, 3 + 3 outer fiber kernels,
     # per middle level Gram + solve (+ FP64 fallback + counter in the
-    # precision form), residual reduction, 2 for ||S||^2, 2 for the test error
+    # precision form), residual reduction, 2 for ||S||^2, 2 for the test error;
+    # a middle level on the grouped Gram runs two kernels for its Gram
     per_level = 4 if prec == bfc.PREC_C64 else 2
-    assert st["launches"] == 12 + (1 + per_level) * p.L
+    n_grouped = prof.get("mid_gram_grp", (0, 0.0))[0] // 2
+    assert st["launches"] == 12 + (1 + per_level) * p.L + n_grouped
 
 
 @pytest.fixture(scope="module")
@@ -231,7 +254,9 @@ def test_grouped_gram_equals_per_entry_gram(request, which, prec):
     p, X0 = request.getfixturevalue(which)
     out = {}
     for gram in (bfc.GRAM_AUTO, bfc.GRAM_CUDA):
-        with make(p, prec, gram_impl=gram) as c:
+        # group_ratio 2: every middle level on the grouped Gram
+        with make(p, prec, gram_impl=gram, group_ratio=2.0) as c:
+            assert all(c.level_groups(m)[1] == (gram == bfc.GRAM_AUTO) for m in range(1, p.L + 1))
             c.set_factors(X0)
             st = c.sweep()
             out[gram] = (c.get_factors(), st)
