@@ -352,7 +352,9 @@ static bfc_status build(Ctx* c, const Inputs& in)
         int64_t gmax = 0;
         for (const GroupLevel& gl : c->grp)
             if (gl.gstart) gmax = std::max(gmax, gl.ngroups);
-        if (gmax > 0) BFC_TRY(dalloc(c, &c->grec, (size_t)gmax * (2 * r + r * r) * c->vsz, "group records"));
+        // record [s | M (with 64 bytes between its two row halves) | v]
+        const size_t rec_vals = (size_t)(2 * r + r * r) + 64 / c->vsz;
+        if (gmax > 0) BFC_TRY(dalloc(c, &c->grec, (size_t)gmax * rec_vals * c->vsz, "group records"));
     }
     const size_t fbb = ops->fallback_bytes(S);
     if (fbb > 0 && L > 0) {

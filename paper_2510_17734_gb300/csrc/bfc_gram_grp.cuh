@@ -67,6 +67,18 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem_src) : "memory");
 }
 
+// Group record [s | M | v] of rank R in values of type V: s at 0, M[c][c']
+// at R + grp_m(c, c'), v at VOFF.  The rows c >= R/2 of M sit 64 bytes
+// further on, so the 4 x 4 blocks of M the Gram tiles read at once (rows
+// 0..3 and 4..7, column blocks 0 and 4) fall into distinct shared-memory
+// banks.
+template <typename V, int R> struct GrpRec {
+    static constexpr int PAD = (int)(64 / sizeof(V));
+    static constexpr int VOFF = R + R * R + PAD;
+    static constexpr int RS = VOFF + R;
+    __host__ __device__ static constexpr int m(int c, int cc) { return R + c * R + cc + (c >= R / 2 ? PAD : 0); }
+};
+
 // Shared-memory budget of k_group_sums: a block's entries (rows of the
 // summed side and values) are staged when they fit.
 template <typename T, int R> struct GsumCfg {
@@ -96,7 +108,8 @@ k_group_sums(const typename cvec<T>::type* __restrict__ H, const typename cvec<T
 {
     typedef typename cvec<T>::type V;
     typedef GsumCfg<T, R> C;
-    constexpr int RS = 2 * R + R * R;
+    typedef GrpRec<V, R> RL;
+    constexpr int RS = RL::RS;
     extern __shared__ __align__(16) unsigned char smem[];
     V* su = (V*)smem;                          // [CAP][R] rows
     V* st = su + (size_t)C::CAP * R;           // [CAP] values
@@ -181,13 +194,13 @@ k_group_sums(const typename cvec<T>::type* __restrict__ H, const typename cvec<T
             m.x -= mc[q][0];
             m.y -= mc[q][1];
         }
-        o[R + a * R + q] = m;
+        o[RL::m(a, q)] = m;
     }
     if constexpr (sizeof(T) == 4) {
         vs.x -= vc[0];
         vs.y -= vc[1];
     }
-    o[R + R * R + a] = vs;
+    o[RL::VOFF + a] = vs;
 }
 
 // acc += x * y.  Precision form: (s, c) is a Kahan pair per component and
@@ -207,6 +220,52 @@ __device__ __forceinline__ void grp_acc(float2& s, float2& c, float2 x, float2 y
 }
 __device__ __forceinline__ void grp_acc(double2& s, double2&, double2 x, double2 y) { cmac(s, x, y); }
 
+// Packed (re, im) pairs of FP32 values and the f32x2 arithmetic of sm_100
+// and later: one instruction acts on both components.
+__device__ __forceinline__ uint64_t g2pack(float a, float b)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 g2unpack(uint64_t r)
+{
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ uint64_t g2fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t g2add(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t g2sub(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// (s, nc) += x y with packed operands: X1 = (x.re, x.re), X2 = (x.im, x.im),
+// Y = (y.re, y.im), Yr = i y = (-y.im, y.re), so x y = X1 Y + X2 Yr.  s is
+// the Kahan sum and nc its negated compensation (the value is s + nc); the
+// compensation enters inside the fused multiply-adds.
+__device__ __forceinline__ void grp_acc2(uint64_t& s, uint64_t& nc, uint64_t X1, uint64_t X2, uint64_t Y,
+                                         uint64_t Yr)
+{
+    const uint64_t q = g2fma(X1, Y, g2fma(X2, Yr, nc));   // x y - c
+    const uint64_t t = g2add(s, q);
+    nc = g2sub(q, g2sub(t, s));
+    s = t;
+}
+
 template <typename T, int R> struct GrpCfg {
     static_assert(R == 4 || R == 8, "grouped Gram tiles need R in {4, 8}");
     static constexpr int D = R * R;
@@ -225,7 +284,8 @@ template <typename T, int R> struct GrpCfg {
     static constexpr int YPT = YSPARE ? (D + NY - 1) / NY : 0;
     static constexpr int NST = 3;                          // ring stages
     static constexpr int NPK = D * (D + 1) / 2;
-    static constexpr int RS = 2 * R + D;                   // group record [s | M | v]
+    typedef GrpRec<typename cvec<T>::type, R> RL;
+    static constexpr int RS = RL::RS;                      // group record [s | M | v]
     static constexpr size_t VS = sizeof(typename cvec<T>::type);
     static constexpr int PIECES = (int)(RS * VS / 16);     // 16-byte pieces per record
     static_assert(RS * VS % 16 == 0, "records must be whole 16-byte pieces");
@@ -253,6 +313,7 @@ k_mid_gram_grp(const typename cvec<T>::type* __restrict__ grec, const int32_t* _
     typedef GrpCfg<T, R> C;
     constexpr int D = C::D, NPK = C::NPK, CG = C::CG, NTH = C::NTH, RS = C::RS, NST = C::NST;
     extern __shared__ __align__(16) unsigned char smem[];
+    typedef typename C::RL RL;
     V* ring = (V*)smem;                           // [NST][CG][RS]
     double2* Kacc = (double2*)(smem + C::RING);   // thread-group reduction (G > 1)
 
@@ -283,12 +344,18 @@ k_mid_gram_grp(const typename cvec<T>::type* __restrict__ grec, const int32_t* _
         // tiles: s_/c_ (Kahan pairs); right-hand side: ys/yc (diagonal tiles
         // or spare threads)
         V s_[4][4], c_[4][4], ys[4], yc[4];
+        uint64_t s2[4][4], n2[4][4];   // complex64 tiles: packed Kahan sums, negated compensations
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             ys[u] = czero<V>();
             yc[u] = czero<V>();
 #pragma unroll
-            for (int v = 0; v < 4; ++v) { s_[u][v] = czero<V>(); c_[u][v] = czero<V>(); }
+            for (int v = 0; v < 4; ++v) {
+                s_[u][v] = czero<V>();
+                c_[u][v] = czero<V>();
+                s2[u][v] = 0ull;
+                n2[u][v] = 0ull;
+            }
         }
         __syncthreads();  // previous slice done with the ring and Kacc
 #pragma unroll
@@ -304,7 +371,57 @@ k_mid_gram_grp(const typename cvec<T>::type* __restrict__ grec, const int32_t* _
             cp_async_commit();
             const V* buf = ring + (size_t)(c % NST) * CG * RS;
             const int cnt = min(CG, g1 - g0 - c * CG);
-            if (worker) {
+            if constexpr (sizeof(T) == 4) {
+              if (worker) {
+                for (int gi = grp; gi < cnt; gi += C::G) {
+                    const V* gr = buf + gi * RS;
+                    if constexpr (!BY_COL) {
+                        // X = conj(h) h^T from s = h; Y = M (sums of the w side)
+                        const V x = cmul(make_conj(gr[aI]), gr[aJ]);
+                        const uint64_t X1 = g2pack(x.x, x.x), X2 = g2pack(x.y, x.y);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            V yr[4];
+                            load4(yr, gr + RL::m(cI + u, cJ));
+#pragma unroll
+                            for (int v = 0; v < 4; ++v)
+                                grp_acc2(s2[u][v], n2[u][v], X1, X2, g2pack(yr[v].x, yr[v].y),
+                                         g2pack(-yr[v].y, yr[v].x));
+                        }
+                        if (diag) {
+                            const V xv = make_conj(gr[aI]);
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) grp_acc(ys[u], yc[u], xv, gr[RL::VOFF + cI + u]);
+                        }
+                    } else {
+                        // X = M (sums of the h side); Y = conj(w) w^T from s = w:
+                        // term (u, v) = (conj(s_cI+u) x) s_cJ+v
+                        const V x = gr[RL::m(aI, aJ)];
+                        V sj[4], si[4];
+                        load4(sj, gr + cJ);
+                        load4(si, gr + cI);
+                        uint64_t Y[4], Q[4];
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            Y[v] = g2pack(sj[v].x, sj[v].y);
+                            Q[v] = g2pack(-sj[v].y, sj[v].x);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const V xa = cmul(make_conj(si[u]), x);
+                            const uint64_t X1 = g2pack(xa.x, xa.x), X2 = g2pack(xa.y, xa.y);
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) grp_acc2(s2[u][v], n2[u][v], X1, X2, Y[v], Q[v]);
+                        }
+                        if (diag) {
+                            const V xv = gr[RL::VOFF + aI];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) grp_acc(ys[u], yc[u], xv, make_conj(si[u]));
+                        }
+                    }
+                }
+              }
+            } else if (worker) {
                 for (int gi = grp; gi < cnt; gi += C::G) {
                     const V* gr = buf + gi * RS;
                     if constexpr (!BY_COL) {
@@ -313,18 +430,18 @@ k_mid_gram_grp(const typename cvec<T>::type* __restrict__ grec, const int32_t* _
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             V yr[4];
-                            load4(yr, gr + R + (cI + u) * R + cJ);
+                            load4(yr, gr + RL::m(cI + u, cJ));
 #pragma unroll
                             for (int v = 0; v < 4; ++v) grp_acc(s_[u][v], c_[u][v], x, yr[v]);
                         }
                         if (diag) {
                             const V xv = make_conj(gr[aI]);
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) grp_acc(ys[u], yc[u], xv, gr[R + D + cI + u]);
+                            for (int u = 0; u < 4; ++u) grp_acc(ys[u], yc[u], xv, gr[RL::VOFF + cI + u]);
                         }
                     } else {
                         // X = M (sums of the h side); Y = conj(w) w^T from s = w
-                        const V x = gr[R + aI * R + aJ];
+                        const V x = gr[RL::m(aI, aJ)];
                         V sj[4], si[4];
                         load4(sj, gr + cJ);
                         load4(si, gr + cI);
@@ -337,13 +454,14 @@ k_mid_gram_grp(const typename cvec<T>::type* __restrict__ grec, const int32_t* _
                             for (int v = 0; v < 4; ++v) grp_acc(s_[u][v], c_[u][v], a, sj[v]);
                         }
                         if (diag) {
-                            const V xv = gr[R + D + aI];
+                            const V xv = gr[RL::VOFF + aI];
 #pragma unroll
                             for (int u = 0; u < 4; ++u) grp_acc(ys[u], yc[u], xv, make_conj(si[u]));
                         }
                     }
                 }
-            } else if (ythread) {
+            }
+            if (ythread) {
                 // y[(a, c)] += xv[a] yv[c] for p = yb + NY x
                 for (int gi = 0; gi < cnt; ++gi) {
                     const V* gr = buf + gi * RS;
@@ -352,8 +470,8 @@ k_mid_gram_grp(const typename cvec<T>::type* __restrict__ grec, const int32_t* _
                         const int p = yb + C::NY * x;
                         if (p < D) {
                             const int a = p / R, cc = p - (p / R) * R;
-                            const V xv = BY_COL ? gr[R + D + a] : make_conj(gr[a]);
-                            const V yv = BY_COL ? make_conj(gr[cc]) : gr[R + D + cc];
+                            const V xv = BY_COL ? gr[RL::VOFF + a] : make_conj(gr[a]);
+                            const V yv = BY_COL ? make_conj(gr[cc]) : gr[RL::VOFF + cc];
                             grp_acc(ys[x], yc[x], xv, yv);
                         }
                     }
@@ -366,8 +484,9 @@ k_mid_gram_grp(const typename cvec<T>::type* __restrict__ grec, const int32_t* _
             for (int u = 0; u < 4; ++u) {
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
-                    s_[u][v].x = __fsub_rn(s_[u][v].x, c_[u][v].x);
-                    s_[u][v].y = __fsub_rn(s_[u][v].y, c_[u][v].y);
+                    const float2 t = g2unpack(g2add(s2[u][v], n2[u][v]));
+                    s_[u][v].x = t.x;
+                    s_[u][v].y = t.y;
                 }
                 ys[u].x = __fsub_rn(ys[u].x, yc[u].x);
                 ys[u].y = __fsub_rn(ys[u].y, yc[u].y);
