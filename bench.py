@@ -367,9 +367,10 @@ def oracle_sample(prob, frac_every: int):
 def run_batched(bfc_mod, count=64, max_sweeps=20, tol=1e-4):
     """The batched workload (64 independent problems, n in 1024..16384,
     r in {4, 6, 8}, |Omega| = c n log2 n, c in [4, 8]) in the precision form
-    through bfc_batch_complete: low-rank starts, then rounds of graph-replayed
-    sweeps on per-problem streams until each problem's training error is
-    below tol or max_sweeps ran; Gram kernel autotuned per rank."""
+    through bfc_batch_complete: low-rank starts, the per-rank Gram autotuning,
+    then every remaining sweep of every problem in one graph launch (a
+    conditional loop per problem that stops at its training tolerance or
+    max_sweeps)."""
     import synth
     probs = synth.batch_problems(count)
     cs = [bfc_mod.Completion(p.n, p.L, p.b, p.r, p.lam, p.i, p.j, p.t, p.it, p.jt, p.tt,
@@ -401,54 +402,60 @@ def run_batched(bfc_mod, count=64, max_sweeps=20, tol=1e-4):
             "test_rel_err_median": test[len(test) // 2], "test_rel_err_max": test[-1]}
 
 
-def batch_vs_fp64(bfc_mod, count=16, max_sweeps=30, tol_train=1e-4, tol_c64=3e-4, refine=2):
-    """Time for a batch of problems to reach training error tol_train: the
-    batched precision form (bfc_batch_complete: complex64 sweeps to
-    tol_c64, then `refine` FP64 refinement sweeps) against plain FP64 ALS run
-    problem by problem (bfc_complete to tol_train), same starts.  Problems:
-    n in {1024, 2048, 4096}, r in {4, 6, 8}, the cfg-4 operator family with the
-    paper's sampling rule 6 r n log2 n (the c n log2 n, c in [4, 8] draws are
-    information-limited)."""
+def batch_vs_fp64(bfc_mod, count=16, max_sweeps=30, tol_train=5e-4):
+    """Time for a batch of problems to reach test error 1e-3, three arms from
+    the same low-rank starts and with the same stop rule (training error
+    below tol_train, at which these noise-free problems' test errors are
+    below 1e-3; the count that made it is reported per arm):
+      batched   the precision form through bfc_batch_complete (all sweeps in
+                one graph launch after the per-rank autotuning);
+      sequential the same precision form, problem by problem (bfc_complete):
+                the gain of batching itself;
+      plain_fp64 FP64 ALS problem by problem (bfc_complete).
+    Problems: n in {1024, 2048, 4096}, r in {4, 6, 8}, the cfg-4 operator
+    family with the paper's sampling rule 6 r n log2 n (the c n log2 n,
+    c in [4, 8] draws are information-limited)."""
     import synth
     probs = synth.batch_problems(count, seed_base=synth.BATCH_SEED_BASE + 0x8000,
                                  n_choices=(1024, 2048, 4096), paper_rule=True)
 
     def make(p, prec, q):
-        c64 = prec == bfc_mod.PREC_C64
         return bfc_mod.Completion(p.n, p.L, p.b, p.r, p.lam, p.i, p.j, p.t, p.it, p.jt, p.tt, prec=prec,
-                                  max_sweeps=max_sweeps, tol=tol_c64 if c64 else tol_train, seed=4242 + q,
-                                  init_kind=1, lr_sweeps=10, refine_sweeps=refine if c64 else 0)
+                                  max_sweeps=max_sweeps, tol=tol_train, seed=4242 + q,
+                                  init_kind=1, lr_sweeps=10)
+
+    def summary(last, seconds):
+        te = [st["test_rel_err"] for st in last]
+        return {"seconds": seconds, "test_err_below_1e-3": int(sum(e < 1e-3 for e in te)),
+                "test_err_median": float(np.median(te)), "test_err_max": float(np.max(te)),
+                "sweeps_median": float(np.median([st["sweep"] for st in last]))}
 
     cs = [make(p, bfc_mod.PREC_C64, q) for q, p in enumerate(probs)]
     try:
         t0 = time.perf_counter()
-        last = bfc_mod.batch_complete(cs)
+        last = bfc_mod.batch_complete(cs)   # synchronous
         t_batch = time.perf_counter() - t0
     finally:
         for c in cs:
             c.close()
-    t_fp64, last64 = 0.0, []
-    for q, p in enumerate(probs):
-        c = make(p, bfc_mod.PREC_FP64, q)
-        try:
-            t0 = time.perf_counter()
-            hist = c.complete()
-            t_fp64 += time.perf_counter() - t0
-            last64.append(hist[-1])
-        finally:
-            c.close()
-    te = [st["test_rel_err"] for st in last]
-    te64 = [st["test_rel_err"] for st in last64]
+    arms = {"batched": summary(last, t_batch)}
+    arms["batched"]["graph_launches_after_autotune"] = int(max(st["batch_launches"] for st in last))
+    for name, prec in (("sequential", bfc_mod.PREC_C64), ("plain_fp64", bfc_mod.PREC_FP64)):
+        t, lst = 0.0, []
+        for q, p in enumerate(probs):
+            c = make(p, prec, q)
+            try:
+                t0 = time.perf_counter()
+                lst.append(c.complete()[-1])
+                t += time.perf_counter() - t0
+            finally:
+                c.close()
+        arms[name] = summary(lst, t)
     return {"problems": count, "entries_total": int(sum(p.nnz for p in probs)),
-            "stop": f"plain FP64: training error < {tol_train} or {max_sweeps} sweeps; batched: complex64 "
-                    f"sweeps to training error < {tol_c64} (or {max_sweeps}), then {refine} FP64 sweeps",
-            "batched_precision_form_seconds": t_batch, "plain_fp64_sequential_seconds": t_fp64,
-            "speedup": t_fp64 / t_batch,
-            "test_err_below_1e-3": {"batched": int(sum(e < 1e-3 for e in te)),
-                                    "plain_fp64": int(sum(e < 1e-3 for e in te64))},
-            "test_err_median": {"batched": float(np.median(te)), "plain_fp64": float(np.median(te64))},
-            "sweeps_median": {"batched": float(np.median([st["sweep"] for st in last])),
-                              "plain_fp64": float(np.median([st["sweep"] for st in last64]))}}
+            "stop": f"training error < {tol_train} or {max_sweeps} sweeps (every arm); no FP64 refinement sweeps",
+            "arms": arms,
+            "speedup_vs_plain_fp64": arms["plain_fp64"]["seconds"] / arms["batched"]["seconds"],
+            "speedup_of_batching": arms["sequential"]["seconds"] / arms["batched"]["seconds"]}
 
 
 def run_learned(bfc_mod, n_train=64, n_test=8, epochs=2500, max_sweeps=30, tol=1e-3, c_obs=36, with_nn=False):

@@ -144,6 +144,9 @@ typedef struct {
                                precision form (levels not on the grouped
                                Gram): 0 tensor cores, 1 CUDA cores; -1 FP64
                                path                                         */
+    int32_t batch_launches; /* bfc_batch_complete: graph launches that ran
+                               the sweeps after the autotuning (1: all of
+                               them in one launch); 0 elsewhere             */
 } bfc_sweep_stats;
 
 typedef struct {

@@ -77,7 +77,7 @@ class SweepStats(ctypes.Structure):
                 ("sweep_ms", ctypes.c_double), ("entries_per_s", ctypes.c_double),
                 ("singular_slices", ctypes.c_int64), ("refined_fallbacks", ctypes.c_int64),
                 ("refine_steps", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("gram_impl", ctypes.c_int32)]
+                ("gram_impl", ctypes.c_int32), ("batch_launches", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

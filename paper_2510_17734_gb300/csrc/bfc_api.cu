@@ -455,6 +455,7 @@ static bfc_status collect_stats(Ctx* c, bfc_sweep_stats* out, float ms)
         out->singular_slices = (int64_t)hc[0];
         out->refined_fallbacks = (int64_t)hc[1];
         out->refine_steps = (int64_t)hc[2];
+        out->batch_launches = 0;
     }
     if (!isfinite(hs[0])) return fail(c, BFC_ENONFINITE, "training residual is not finite");
     return BFC_OK;
@@ -1270,6 +1271,171 @@ bfc_status bfc_init_learned(bfc_ctx* ctx, bfc_mlp* model, double omega, double o
     return sync(c);
 }
 
+}  // extern "C"
+
+// Batched completion in one launch: per problem, a conditional WHILE graph
+// node whose body is the problem's captured sweep followed by k_batch_step,
+// which turns the sweep's device scalars into its statistics (the host
+// formulas of collect_stats), stores them in the problem's history and
+// decides on the device whether the loop goes on (train error >= tol,
+// fewer than max_sweeps sweeps, finite residual, no expired device wait).
+// The loop count is bounded by max_sweeps.
+struct BatchSlot {
+    double* hist;      // [max_sweeps][8]: train err, test err, objective, singular, fallbacks, refine steps, wait flag
+    int32_t* nsweeps;  // sweeps done by the launch
+};
+
+__global__ void k_batch_step(cudaGraphConditionalHandle h, const double* __restrict__ sc,
+                             const unsigned long long* __restrict__ cnt, BatchSlot slot, int max_sweeps, double tol,
+                             double lambda, int has_test)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int d = *slot.nsweeps;
+    const double tr = sc[1] > 0 ? sqrt(sc[0] / sc[1]) : sqrt(sc[0]);
+    const double te = has_test ? (sc[4] > 0 ? sqrt(sc[3] / sc[4]) : sqrt(sc[3])) : -1.0;
+    double* hr = slot.hist + (size_t)(d < max_sweeps ? d : max_sweeps - 1) * 8;
+    hr[0] = tr;
+    hr[1] = te;
+    hr[2] = 0.5 * sc[0] + 0.5 * lambda * sc[2];
+    hr[3] = (double)cnt[0];
+    hr[4] = (double)cnt[1];
+    hr[5] = (double)cnt[2];
+    hr[6] = (double)cnt[5];
+    *slot.nsweeps = d + 1;
+    const bool go = d + 1 < max_sweeps && !(tr < tol) && isfinite(sc[0]) && cnt[5] == 0;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// Runs the remaining sweeps of the active problems as one graph launch.
+// Returns BFC_OK with *ran = false (nothing launched) when the graph cannot
+// be built (the caller then runs the sweeps round by round).
+static bfc_status batch_one_launch(std::vector<Ctx*>& cs, std::vector<char>& active, std::vector<int>& done,
+                                   std::vector<bfc_sweep_stats>& st, bool* ran)
+{
+    *ran = false;
+    const int32_t count = (int32_t)cs.size();
+    std::vector<int32_t> rem((size_t)count, 0), off((size_t)count + 1, 0);
+    for (int32_t q = 0; q < count; ++q) {
+        rem[q] = active[q] ? std::max(cs[q]->P.max_sweeps - done[q], 0) : 0;
+        if (rem[q] > 0 && !cs[q]->sweep_graph_src) return BFC_OK;
+        off[q + 1] = off[q] + rem[q];
+    }
+    if (off[count] == 0) return BFC_OK;
+    double* dh = nullptr;
+    int32_t* dn = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaStream_t bs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+        if (bs) cudaStreamDestroy(bs);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (dh) cudaFree(dh);
+        if (dn) cudaFree(dn);
+    };
+    cudaError_t e = cudaMalloc(&dh, (size_t)off[count] * 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dn, (size_t)count * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(dn, 0, (size_t)count * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(nullptr, BFC_ECUDA, std::string("batch launch set-up: ") + cudaGetErrorString(e));
+    }
+    // graph construction: a failure here leaves the rounds to the caller
+    bool built = true;
+    for (int32_t q = 0; q < count && built; ++q) {
+        if (rem[q] == 0) continue;
+        Ctx* c = cs[q];
+        cudaGraphConditionalHandle h;
+        built = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn = nullptr;
+        if (built) built = cudaGraphAddNode(&cn, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+        if (!built) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraphNode_t sweep = nullptr, step = nullptr;
+        built = cudaGraphAddChildGraphNode(&sweep, body, nullptr, 0, c->sweep_graph_src) == cudaSuccess;
+        BatchSlot slot{dh + (size_t)off[q] * 8, dn + q};
+        int maxs = rem[q];
+        double tol = c->P.tol, lam = c->P.lambda;
+        int has_test = c->NT > 0 ? 1 : 0;
+        const double* sc = c->d_scalars;
+        const unsigned long long* cnt = c->d_count;
+        void* args[] = {&h, &sc, &cnt, &slot, &maxs, &tol, &lam, &has_test};
+        cudaKernelNodeParams kp = {};
+        kp.func = (void*)k_batch_step;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(32);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        if (built) built = cudaGraphAddKernelNode(&step, body, &sweep, 1, &kp) == cudaSuccess;
+    }
+    if (built) built = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+    if (!built) {
+        cudaGetLastError();
+        cleanup();
+        return BFC_OK;
+    }
+    e = cudaEventRecord(e0, bs);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, bs);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, bs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(bs);
+    std::vector<double> hh((size_t)off[count] * 8);
+    std::vector<int32_t> hn((size_t)count);
+    if (e == cudaSuccess) e = cudaMemcpy(hh.data(), dh, hh.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hn.data(), dn, hn.size() * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cleanup();
+    if (e != cudaSuccess) return fail(nullptr, BFC_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    *ran = true;
+    int32_t rounds = 1;
+    for (int32_t q = 0; q < count; ++q) rounds = std::max(rounds, hn[q]);
+    for (int32_t q = 0; q < count; ++q) {
+        if (rem[q] == 0) continue;
+        Ctx* c = cs[q];
+        const int32_t d = std::min(hn[q], rem[q]);
+        c->sweeps_done += d;
+        c->n_launch += (int64_t)d * (c->graph_launches + 1);
+        done[q] += d;
+        active[q] = 0;
+        if (d <= 0) continue;
+        const double* hr = hh.data() + (size_t)(off[q] + d - 1) * 8;
+        bfc_sweep_stats& o = st[q];
+        o.sweep = c->sweeps_done;
+        o.train_rel_err = hr[0];
+        o.test_rel_err = hr[1];
+        o.objective = hr[2];
+        o.sweep_ms = ms / rounds;   // the launch's time per round of sweeps
+        o.entries_per_s = o.sweep_ms > 0 ? (double)c->N / (o.sweep_ms * 1e-3) : 0.0;
+        o.singular_slices = (int64_t)hr[3];
+        o.refined_fallbacks = (int64_t)hr[4];
+        o.refine_steps = (int64_t)hr[5];
+        o.launches = (int64_t)d * (c->graph_launches + 1);
+        o.gram_impl = c->fp32 ? (c->gram_tc ? 0 : 1) : -1;
+        o.batch_launches = 1;
+        if (hr[6] != 0.0) {
+            cudaMemsetAsync(c->d_count + 5, 0, sizeof(unsigned long long), c->stream);
+            sync(c);
+            return fail(c, BFC_ETIMEOUT, "a bounded device wait expired (tensor-core Gram or bulk copy)");
+        }
+        if (!isfinite(hr[0])) return fail(c, BFC_ENONFINITE, "training residual is not finite");
+    }
+    return BFC_OK;
+}
+
+extern "C" {
+
 bfc_status bfc_batch_complete(int32_t count, bfc_ctx* const* ctxs, bfc_sweep_stats* last)
 {
     if (count < 0 || (count > 0 && !ctxs)) return fail(nullptr, BFC_EINVAL, "bad batch arguments");
@@ -1328,6 +1494,14 @@ bfc_status bfc_batch_complete(int32_t count, bfc_ctx* const* ctxs, bfc_sweep_sta
             const bfc_status s2 = capture_sweep(cs[q]);
             if (s2 != BFC_OK) return bad(cs[q], s2);
         }
+    // all remaining sweeps as one launch (conditional WHILE nodes); the
+    // rounds below run only where that graph cannot be built
+    {
+        bool ran = false;
+        const bfc_status sl = batch_one_launch(cs, active, done, st, &ran);
+        if (sl != BFC_OK) return sl;
+    }
+    int32_t nrounds = 0;
     cudaStream_t bs = nullptr;
     cudaGraphExec_t round = nullptr;
     std::vector<char> round_set;
@@ -1347,6 +1521,7 @@ bfc_status bfc_batch_complete(int32_t count, bfc_ctx* const* ctxs, bfc_sweep_sta
                 all_graphs = all_graphs && cs[q]->sweep_graph_src != nullptr;
             }
         if (!any) break;
+        ++nrounds;
         if (all_graphs) {
             std::vector<char> want(active.begin(), active.end());
             if (!round || want != round_set) {
@@ -1402,6 +1577,7 @@ bfc_status bfc_batch_complete(int32_t count, bfc_ctx* const* ctxs, bfc_sweep_sta
                 return bad(c, s4);
             }
             done[q] += 1;
+            st[q].batch_launches = nrounds;
             if (stop(q)) active[q] = 0;
         }
     }

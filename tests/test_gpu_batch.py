@@ -48,6 +48,8 @@ def test_batch_equals_individual_runs_bitwise():
             np.testing.assert_array_equal(c.get_factors(), X)
             assert last[q]["train_rel_err"] == st["train_rel_err"]
             assert last[q]["launches"] > 0
+            # all six sweeps of every problem ran in one graph launch
+            assert last[q]["batch_launches"] == 1
     finally:
         for c in batch:
             c.close()
@@ -64,6 +66,7 @@ def test_batch_autotuned_reaches_the_same_errors():
         last = bfc.batch_complete(batch)
         for q in range(len(probs)):
             assert last[q]["sweep"] == 6
+            assert last[q]["batch_launches"] == 1
             assert abs(last[q]["train_rel_err"] - ref[q]) <= 1e-3 * ref[q]
             assert last[q]["gram_impl"] == (-1 if PRECS[q] == bfc.PREC_FP64 else last[q]["gram_impl"])
             assert last[q]["gram_impl"] in ((-1,) if PRECS[q] == bfc.PREC_FP64 else (0, 1))
