@@ -358,6 +358,64 @@ def time_to_tolerance(bfc_mod, prec, tol=1e-3, max_sweeps=30):
             "nnz_train": prob.nnz, "test_rel_err": [float(f"{e:.3e}") for e in errs]}
 
 
+def run_config_table(bfc_mod, tol=1e-3):
+    """The small single-problem configurations (n = 256: plain ALS, 10
+    sweeps; n = 4096 with 1e-4 noise: ALS, 20 sweeps, and L-BFGS, 200
+    iterations) for the plain FP64 path and the precision form: ms per
+    sweep (library CUDA events), entries/s, time to test error tol (wall,
+    from the start of the low-rank completion, 10 sweeps of Alg. 1 with
+    L = 0), final test error; and the oracle's whole sweep on one host
+    thread and on all of them."""
+    import oracle
+    import synth
+    oracle.build()
+    cores = host_cores()
+    out = {}
+    for k, iters in ((1, 10), (2, 20)):
+        p = synth.config(k)
+        A0, B0 = synth.random_lowrank_start(p, p.r)
+        row = {"workload": f"n={p.n} L={p.L} b={p.b} r={p.r}, {p.nnz} train entries", "nnz_train": p.nnz}
+        X0 = None
+        for name, prec in (("plain_fp64", bfc_mod.PREC_FP64), ("precision_form", bfc_mod.PREC_C64)):
+            c = bfc_mod.Completion(p.n, p.L, p.b, p.r, p.lam, p.i, p.j, p.t, p.it, p.jt, p.tt, prec=prec)
+            try:
+                t0 = time.perf_counter()
+                c.lowrank_init(A0, B0, 10)
+                if X0 is None:
+                    X0 = c.get_factors()
+                errs, ms, reached = [], [], None
+                for _ in range(iters):
+                    st = c.sweep()
+                    errs.append(st["test_rel_err"])
+                    ms.append(st["sweep_ms"])
+                    if reached is None and st["test_rel_err"] < tol:
+                        reached = time.perf_counter() - t0
+                med = float(np.median(ms))
+                row[name] = {"ms_per_sweep": med, "entries_per_s": p.nnz / (med * 1e-3),
+                             "seconds_to_tol": reached, "final_test_rel_err": errs[-1],
+                             "test_rel_err": [float(f"{e:.3e}") for e in errs]}
+            finally:
+                c.close()
+        if k == 2:
+            for name, prec in (("lbfgs_plain_fp64", bfc_mod.PREC_FP64), ("lbfgs_precision_form", bfc_mod.PREC_C64)):
+                c = bfc_mod.Completion(p.n, p.L, p.b, p.r, p.lam, p.i, p.j, p.t, p.it, p.jt, p.tt, prec=prec)
+                try:
+                    t0 = time.perf_counter()
+                    c.lowrank_init(A0, B0, 10)
+                    hist = c.lbfgs(200)
+                    wall = time.perf_counter() - t0
+                    te = [h["test_rel_err"] for h in hist]
+                    row[name] = {"iterations": len(hist), "seconds": wall, "final_test_rel_err": te[-1],
+                                 "best_test_rel_err": min(te)}
+                finally:
+                    c.close()
+        m1, t1 = time_oracle_sweep(p, X0, 1, threads=1)
+        mall, tall = time_oracle_sweep(p, X0, 1, threads=cores)
+        row["cpu_oracle"] = {"serial_s_per_sweep": t1, "all_cores_s_per_sweep": tall, "cores": cores}
+        out[f"config{k}"] = row
+    return out
+
+
 def oracle_sample(prob, frac_every: int):
     """Every `frac_every`-th training entry of the workload."""
     sel = np.arange(0, prob.nnz, frac_every)
@@ -476,10 +534,16 @@ def run_learned(bfc_mod, n_train=64, n_test=8, epochs=2500, max_sweeps=30, tol=1
     base = synth.BATCH_SEED_BASE + 0x10000
     rng = synth.SplitMix64(base + synth.SEED_PARAMS)
 
+    shared = {}
+
     def problem(q):
         u = rng.uniform(2)
         om, h = 1 / 16 + u[0] * (1 / 4 - 1 / 16), 0.5 + 1.5 * u[1]
-        return om, h, synth.make_problem(f"learned{q}", n, L, b, r, om * math.pi * n, h, nobs, 1e-7, 15, base)
+        if "base" not in shared:   # the sample positions, drawn once for the family
+            shared["base"] = synth.make_problem(f"learned{q}", n, L, b, r, om * math.pi * n, h, nobs, 1e-7, 15,
+                                                base)
+            return om, h, shared["base"]
+        return om, h, synth.family_member(shared["base"], f"learned{q}", om * math.pi * n, h)
 
     def completion(p, prec, **kw):
         return bfc_mod.Completion(p.n, p.L, p.b, p.r, p.lam, p.i, p.j, p.t, p.it, p.jt, p.tt, prec=prec, **kw)
@@ -896,7 +960,8 @@ def run_bfc(args, rank, world, local_rank):
     if not args.no_batch and not args.n:
         line["batched"] = run_batched(bfc)
     if not args.no_learned and not args.n:
-        line["learned_start"] = run_learned(bfc, n_train=args.learned_train, epochs=args.learned_epochs)
+        line["learned_start"] = run_learned(bfc, n_train=args.learned_train, n_test=args.learned_test,
+                                            epochs=args.learned_epochs)
 
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -924,6 +989,13 @@ def main():
     ap.add_argument("--no-radon", action="store_true", help="skip the Radon-transform run")
     ap.add_argument("--learned-train", type=int, default=64, help="training completions of the learned start")
     ap.add_argument("--learned-epochs", type=int, default=2500, help="training epochs of the learned start")
+    ap.add_argument("--learned-test", type=int, default=8, help="held-out draws of the learned start")
+    ap.add_argument("--configs-table", action="store_true",
+                    help="measure the n = 256 and n = 4096 configurations (GPU both paths, L-BFGS, oracle) and "
+                         "print their JSON")
+    ap.add_argument("--learned-only", action="store_true",
+                    help="run only the learned-start experiment (its sizes from the --learned-* flags) and print "
+                         "its JSON")
     ap.add_argument("--group-ratio", type=float, default=0.0,
                     help="groups-per-entry threshold of the grouped Gram (0: library default, < 0: never)")
     ap.add_argument("--gram", default="auto", choices=["auto", "tensor", "cuda"],
@@ -938,6 +1010,20 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.configs_table:
+        import paper_2510_17734_gb300 as bfc
+        bfc.load()
+        if rank == 0:
+            print(json.dumps({"configs": run_config_table(bfc)}), flush=True)
+        return 0
+    if args.learned_only:
+        import paper_2510_17734_gb300 as bfc
+        bfc.load()
+        if rank == 0:
+            res = run_learned(bfc, n_train=args.learned_train, n_test=args.learned_test,
+                              epochs=args.learned_epochs)
+            print(json.dumps({"learned_start": res}), flush=True)
+        return 0
     if world > 1:
         import torch
         import torch.distributed as dist

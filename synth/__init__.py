@@ -168,6 +168,17 @@ def make_problem(name: str, n: int, L: int, b: int, r: int, omega: float, h: flo
                    t_clean=clean[:n_train].copy())
 
 
+def family_member(base: Problem, name: str, omega: float, h: float) -> Problem:
+    """A member of `base`'s operator family at the same sample positions
+    (training and test) with the kernel's parameters (omega, h) changed:
+    only the values are recomputed (noise-free)."""
+    tr = helmholtz_line(base.n, omega, h, base.i, base.j)
+    te = helmholtz_line(base.n, omega, h, base.it, base.jt)
+    return Problem(name=name, n=base.n, L=base.L, b=base.b, r=base.r, omega=omega, h=h, lam=base.lam,
+                   sweeps=base.sweeps, seed=base.seed, i=base.i, j=base.j, t=tr, it=base.it, jt=base.jt,
+                   tt=te, t_clean=tr)
+
+
 def config(index: int, n_override: int | None = None) -> Problem:
     """The single-problem workloads, by 1-based index:
     1  n=256   L=4  b=16 r=4 h=1   omega=pi n/8  |Omega|=8 n log2 n  lambda=1e-8 10 sweeps

@@ -75,3 +75,15 @@ def test_batch_problem_ranges():
         assert p.n in (256, 512) and p.r in (4, 6, 8)
         assert math.pi * p.n / 16 <= p.omega <= math.pi * p.n / 4
         assert 0.5 <= p.h <= 2.0
+
+
+def test_family_member_equals_a_fresh_problem_at_the_same_positions():
+    """A family member (same seed, other omega and h) built from a base
+    problem's positions equals the problem drawn from scratch."""
+    n, L, b, r = 256, 4, 16, 4
+    base = synth.make_problem("a", n, L, b, r, 0.1 * math.pi * n, 1.0, 8 * n * 8, 1e-7, 15, 123)
+    ref = synth.make_problem("b", n, L, b, r, 0.2 * math.pi * n, 1.5, 8 * n * 8, 1e-7, 15, 123)
+    m = synth.family_member(base, "b", 0.2 * math.pi * n, 1.5)
+    for f in ("i", "j", "t", "it", "jt", "tt"):
+        np.testing.assert_array_equal(getattr(m, f), getattr(ref, f))
+    assert (m.omega, m.h) == (ref.omega, ref.h)
