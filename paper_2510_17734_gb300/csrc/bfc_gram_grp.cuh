@@ -40,16 +40,6 @@ template <typename V> __device__ __forceinline__ V make_conj(V a)
     return a;
 }
 
-// u[a] for a runtime index a (a select chain, so u stays in registers).
-template <typename V, int R> __device__ __forceinline__ V pick_row(const V (&u)[R], int a)
-{
-    V out = u[0];
-#pragma unroll
-    for (int q = 1; q < R; ++q)
-        if (q == a) out = u[q];
-    return out;
-}
-
 // 16-byte asynchronous global -> shared copy (L2 only) and its group waits.
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 {
@@ -164,7 +154,7 @@ k_group_sums(const typename cvec<T>::type* __restrict__ H, const typename cvec<T
             const V* row = ub + (size_t)e * R;
 #pragma unroll
             for (int q = 0; q < R; ++q) u[q] = row[q];
-            const V ua = pick_row(u, a);
+            const V ua = row[a];   // one more load instead of a select chain
 #pragma unroll
             for (int q = 0; q < R; ++q) cmacc(mp[q], ua, u[q]);
             cmacc(vp, ua, tb[e]);
