@@ -79,7 +79,7 @@ typedef struct {
     int64_t n;              /* matrix size; must equal b * 2^L               */
     int32_t L;              /* butterfly levels, 0 <= L <= 24 (L = 0: low-rank) */
     int32_t b;              /* leaf size (the paper's c), >= 1               */
-    int32_t r;              /* butterfly rank, 1 <= r <= 10                  */
+    int32_t r;              /* butterfly rank, 1 <= r <= 12                  */
     double lambda;          /* regularization added to every system, >= 0    */
     int32_t prec;           /* bfc_precision                                 */
     int32_t max_sweeps;     /* bfc_complete: sweep limit                     */

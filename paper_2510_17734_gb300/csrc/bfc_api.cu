@@ -371,7 +371,7 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
     if (!params || !out) return fail(nullptr, BFC_EINVAL, "null argument");
     const bfc_params& p = *params;
     if (!valid_sizes(p.n, p.L, p.b, p.r))
-        return fail(nullptr, BFC_EINVAL, "invalid sizes: need n = b * 2^L, 0 <= L <= 24, 1 <= r <= 10");
+        return fail(nullptr, BFC_EINVAL, "invalid sizes: need n = b * 2^L, 0 <= L <= 24, 1 <= r <= 12");
     if (!(p.lambda >= 0.0) || !isfinite(p.lambda)) return fail(nullptr, BFC_EINVAL, "lambda must be finite and >= 0");
     if (!isfinite(p.ridge_rel)) return fail(nullptr, BFC_EINVAL, "ridge_rel must be finite");
     if (p.prec != BFC_PREC_FP64 && p.prec != BFC_PREC_C64_FP64SOLVE)

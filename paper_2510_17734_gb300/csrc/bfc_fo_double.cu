@@ -1,5 +1,5 @@
 // Dispatch table of the first-order methods and the matrix-vector product
-// for compute type double, ranks 1..10.
+// for compute type double, ranks 1..12.
 #include "bfc_first_order.cuh"
 
 namespace bfc {
@@ -17,6 +17,8 @@ const FoOps* fo_ops_double(int r)
     case 8: return &FoEntry<double, 8>::ops;
     case 9: return &FoEntry<double, 9>::ops;
     case 10: return &FoEntry<double, 10>::ops;
+    case 11: return &FoEntry<double, 11>::ops;
+    case 12: return &FoEntry<double, 12>::ops;
     default: return nullptr;
     }
 }

@@ -1,5 +1,5 @@
 // Dispatch table of the first-order methods and the matrix-vector product
-// for compute type float, ranks 1..10.
+// for compute type float, ranks 1..12.
 #include "bfc_first_order.cuh"
 
 namespace bfc {
@@ -17,6 +17,8 @@ const FoOps* fo_ops_float(int r)
     case 8: return &FoEntry<float, 8>::ops;
     case 9: return &FoEntry<float, 9>::ops;
     case 10: return &FoEntry<float, 10>::ops;
+    case 11: return &FoEntry<float, 11>::ops;
+    case 12: return &FoEntry<float, 12>::ops;
     default: return nullptr;
     }
 }

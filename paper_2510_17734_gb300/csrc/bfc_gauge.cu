@@ -326,6 +326,8 @@ cudaError_t launch_canonicalize(double2* z1, double2* Z, double2* zL, int64_t n,
     case 8: return canon_all<8>(z1, Z, zL, n, L, b, st);
     case 9: return canon_all<9>(z1, Z, zL, n, L, b, st);
     case 10: return canon_all<10>(z1, Z, zL, n, L, b, st);
+    case 11: return canon_all<11>(z1, Z, zL, n, L, b, st);
+    case 12: return canon_all<12>(z1, Z, zL, n, L, b, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -342,6 +344,8 @@ cudaError_t launch_canonicalize(double2* z1, double2* Z, double2* zL, int64_t n,
     case 8: return FN<8>(__VA_ARGS__);              \
     case 9: return FN<9>(__VA_ARGS__);              \
     case 10: return FN<10>(__VA_ARGS__);            \
+    case 11: return FN<11>(__VA_ARGS__);            \
+    case 12: return FN<12>(__VA_ARGS__);            \
     default: return cudaErrorInvalidValue;          \
     }
 

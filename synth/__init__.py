@@ -206,15 +206,15 @@ def config(index: int, n_override: int | None = None) -> Problem:
 RADON_SEED_BASE = 0xBFC20000
 
 
-def radon_problem(n: int = 4096, b: int = 4, r: int = 10, c_obs: float = 70.0, c_test: float = 10.0,
+def radon_problem(n: int = 4096, b: int = 4, r: int = 12, c_obs: float = 70.0, c_test: float = 10.0,
                   lam: float = 1e-8, sweeps: int = 20) -> Problem:
     """The Radon-transform workload of Sec. 5.3: the matrix of radon_1d,
-    leaf size b (the paper's c = 4), rank r, |Omega| = c_obs n log2 n
+    leaf size b (the paper's c = 4), rank estimate r, |Omega| = c_obs n log2 n
     training and |Omega_test| = c_test n log2 n test entries, drawn uniformly
     without replacement (the test entries are the last draws).  The default is
-    the paper's convergence study: n = 4096 (L = 10), 7 r n log2 n =
-    3,440,640 training and r n log2 n = 491,520 test entries with r = 10 (the
-    printed counts; the text's r = 12 is the estimate the completion used)."""
+    the paper's convergence study: n = 4096 (L = 10), rank estimate r = 12,
+    3,440,640 training and 491,520 test entries (the printed counts, which are
+    7 r n log2 n and r n log2 n with the actual rank 10)."""
     L = int(round(math.log2(n // b)))
     if n != b << L:
         raise ValueError("n must equal b * 2^L")

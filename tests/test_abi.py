@@ -52,7 +52,7 @@ def test_create_validates_sizes_before_touching_a_device(lib):
     import numpy as np
     i = np.zeros(4, np.int32)
     t = np.zeros(4, np.complex128)
-    bad = [dict(n=100, L=2, b=16, r=4), dict(n=64, L=2, b=16, r=0), dict(n=64, L=2, b=16, r=11)]
+    bad = [dict(n=100, L=2, b=16, r=4), dict(n=64, L=2, b=16, r=0), dict(n=64, L=2, b=16, r=13)]
     for kw in bad:
         prm = bfc.Params(lam=1e-6, prec=0, **kw)
         with pytest.raises(bfc.BfcError, match="EINVAL"):

@@ -297,6 +297,46 @@ def test_grad_parity(cfg2s, prec, include_reg):
     assert np.abs(gg - go).max() <= TOL[prec] * scale
 
 
+@pytest.fixture(scope="module", params=[11, 12])
+def high_rank(request):
+    # ranks 11 and 12 (12 is the rank estimate of the Radon convergence study,
+    # Sec. 5.3): D = r^2 = 121 / 144 features per middle-level system.  Data
+    # from a planted random butterfly of the same rank, a random start: the
+    # block systems are well determined (about 920 entries per slice)
+    r = request.param
+    n, L, b = 256, 4, 16
+    Xt = synth.random_factors(n, L, r, 500 + r)
+    X0 = synth.random_factors(n, L, r, 600 + r)
+    i, j = synth.draw_pairs(n, 16 * n * 8, 700 + r)
+    t = oracle.eval_entries(n, L, b, r, Xt, i, j)
+    return (n, L, b, r, 1e-8, i, j, t), X0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_one_sweep_and_gradient_parity_high_rank(high_rank, prec):
+    (n, L, b, r, lam, i, j, t), X0 = high_rank
+    Xo, st_o = oracle.als_sweep(n, L, b, r, lam, X0, i, j, t, ridge_rel=RIDGE[prec])
+    go, fo = oracle.grad(n, L, b, r, lam, X0, i, j, t, include_reg=True)
+    with bfc.Completion(n, L, b, r, lam, i, j, t, prec=prec) as c:
+        c.set_factors(X0)
+        gg, fg = c.grad(True)
+        st = c.sweep()
+        Xg = c.get_factors()
+    tol = TOL[prec]
+    assert abs(fg - fo) <= tol * abs(fo)
+    assert np.abs(gg - go).max() <= tol * np.abs(go).max()
+    # rounding amplified by the worst-conditioned block system (kappa_max
+    # about 5e4 / 1.2e5 here: 1e-11 in FP64, 3e-3 / 7e-3 in complex64)
+    kappa = max(float(cs.max()) for cs in block_conditions(X0, Xo, i, j, t, n, L, b, r, lam, RIDGE[prec])
+                if cs.size)
+    tol = max(tol, kappa * (2.0 ** -52 if prec == bfc.PREC_FP64 else 2.0 ** -24))
+    assert abs(st["objective"] - st_o["objective"]) <= tol * abs(st_o["objective"])
+    assert abs(st["train_rel_err"] - st_o["train_rel_err"]) <= tol * st_o["train_rel_err"]
+    xg = oracle.eval_entries(n, L, b, r, Xg, i, j)
+    xo = oracle.eval_entries(n, L, b, r, Xo, i, j)
+    assert rel_dev(xg, xo) <= tol, (rel_dev(xg, xo), tol, kappa)
+
+
 # ------------------------------------------------------------ init paths
 
 @pytest.mark.parametrize("prec", PRECS)
