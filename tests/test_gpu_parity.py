@@ -490,6 +490,32 @@ def cfg3():
     return p, X0, X1, s1, s2
 
 
+def test_full_size_orders_are_stable_sorts():
+    """Every level order at n = 65536 (3.77 M entries): a stable sort by the
+    level key, further by row or column inside the slices of the grouped
+    levels, with the oracle's key formula; group counts per level."""
+    p = synth.config(3)
+    keys = [p.i.astype(np.int64)] + [k.astype(np.int64) for k in level_keys(p.i, p.j, p.L, p.b)] + \
+        [p.j.astype(np.int64)]
+    with bfc.Completion(p.n, p.L, p.b, p.r, p.lam, p.i, p.j, p.t, prec=bfc.PREC_C64) as c:
+        grouped = 0
+        for level in range(p.L + 2):
+            key = keys[level]
+            sub = np.zeros(p.nnz, dtype=np.int64)
+            if 1 <= level <= p.L:
+                other = (p.j if 2 * level > p.L + 1 else p.i).astype(np.int64)
+                ngroups, on = c.level_groups(level)
+                assert ngroups == np.unique(key * p.n + other).size
+                if on:
+                    sub = other
+                    grouped += 1
+            perm, seg = c.order(level)
+            np.testing.assert_array_equal(perm, np.lexsort((sub, key)))
+            K = p.n if level in (0, p.L + 1) else 1 << (p.L + 1)
+            np.testing.assert_array_equal(seg, np.searchsorted(np.sort(key), np.arange(K + 1)))
+        assert grouped == 6   # levels 1-3 and 10-12 have fewer than 0.2 groups per entry
+
+
 def test_full_size_reported_errors_match_oracle(cfg3):
     p, X0, X1, s1, s2 = cfg3
     tr = oracle.rel_err(p.n, p.L, p.b, p.r, X1, p.i, p.j, p.t)
