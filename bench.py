@@ -667,7 +667,7 @@ def run_first_order(bfc_mod, c, prob, hbm_peak, iters=3, nvec=64):
     return out
 
 
-def run_radon(bfc_mod, sweeps=20, fp64_sweeps=2):
+def run_radon(bfc_mod, sweeps=20, fp64_sweeps=2, init_kind=1, lr_rank=0):
     """The Radon-transform workload of Sec. 5.3 at the paper's convergence
     study: n = 4096, leaf size 4 (L = 10), rank estimate 12, 3,440,640
     training and 491,520 test entries (7 r n log2 n and r n log2 n with the
@@ -679,13 +679,13 @@ def run_radon(bfc_mod, sweeps=20, fp64_sweeps=2):
     import synth
     p = synth.radon_problem(sweeps=sweeps)
     out = {"workload": f"radon n={p.n} L={p.L} b={p.b} r={p.r}, |Omega| = 70 n log2 n ({p.nnz} train / "
-                       f"{p.it.size} test), lambda=1e-8, start: rank-{p.r} low-rank completion (10 sweeps), "
-                       "exact embedding"}
+                       f"{p.it.size} test), lambda=1e-8, start: rank-{lr_rank or p.r} low-rank completion "
+                       f"(10 sweeps), {'Alg. 2 conversion' if init_kind == 2 else 'exact embedding'}"}
     for name, prec, ns in (("precision_form", bfc_mod.PREC_C64, sweeps), ("plain_fp64", bfc_mod.PREC_FP64,
                                                                           fp64_sweeps)):
         c = bfc_mod.Completion(p.n, p.L, p.b, p.r, p.lam, p.i, p.j, p.t, p.it, p.jt, p.tt, prec=prec,
-                               max_sweeps=ns, tol=1e-12, seed=p.seed + synth.SEED_INIT, init_kind=1,
-                               lr_sweeps=10)
+                               max_sweeps=ns, tol=1e-12, seed=p.seed + synth.SEED_INIT, init_kind=init_kind,
+                               lr_rank=lr_rank, lr_sweeps=10)
         try:
             t0 = time.perf_counter()
             hist = c.complete()

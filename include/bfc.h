@@ -293,9 +293,10 @@ bfc_status bfc_lowrank_init(bfc_ctx* ctx, int32_t R, int32_t sweeps,
  *  3. The slices of S^{H+1} (z1 when H = 0) are right-multiplied by V W^T.
  * `gaussians` holds the CN(0, 1) sketch matrices, r + p columns each,
  * row-major, packed O_0 (n rows), O_1 .. O_H and O'_1 .. O'_{L-H}
- * (b 2^{L-l} rows each); same memory kind as A and B.  With R <= r and leaf
- * blocks of full column rank the butterfly reproduces A B^T to rounding.
- * EINVAL unless 1 <= R <= r, p >= 0, r + p <= 32 and (L > 0) b >= R. */
+ * (b 2^{L-l} rows each); same memory kind as A and B.  With R <= r the
+ * butterfly reproduces A B^T to rounding; a leaf block smaller than r
+ * (b < r) gets b columns of Q and zeros (its b rows are spanned exactly).
+ * EINVAL unless 1 <= R <= r, p >= 0 and r + p <= 32. */
 bfc_status bfc_lowrank_to_butterfly(bfc_ctx* ctx, int32_t R, const double* A, const double* B, int32_t p,
                                     const double* gaussians);
 

@@ -947,8 +947,6 @@ bfc_status bfc_lowrank_to_butterfly(bfc_ctx* ctx, int32_t R, const double* A, co
     if (!c) return BFC_EINVAL;
     if (R < 1 || R > c->r || p < 0 || c->r + p > 32 || !A || !B || !gaussians)
         return fail(c, BFC_EINVAL, "low-rank to butterfly needs 1 <= R <= r, p >= 0, r + p <= 32 and all arrays");
-    if (c->L > 0 && c->b < R)
-        return fail(c, BFC_EINVAL, "low-rank to butterfly: leaf size b must be >= R");
     if (c->P.values_on_device)
         return lr2bf_into(c, R, (const double2*)A, (const double2*)B, gaussians, cudaMemcpyDeviceToDevice, p);
     // host A, B: staged in a device buffer of the context's own
@@ -1012,7 +1010,6 @@ static bfc_status complete_init(Ctx* c)
         const int p = c->P.lr2bf_oversample > 0 ? c->P.lr2bf_oversample : 5;
         if (c->P.init_kind == 2) {
             if (c->r + p > 32) return fail(c, BFC_EINVAL, "r + lr2bf_oversample must be <= 32");
-            if (c->L > 0 && c->b < R) return fail(c, BFC_EINVAL, "Alg. 2 needs b >= lr_rank");
             uint64_t kg = 0;
             splitmix_cnormal(c->P.seed + 1, kg, lr2bf_gaussian_count(c->n, c->L, c->b, c->r, p), 1.0, G);
         }

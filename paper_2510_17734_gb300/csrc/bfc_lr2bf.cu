@@ -49,12 +49,101 @@ __device__ __forceinline__ double wsum(double v)
 }
 __device__ __forceinline__ double2 wsum2(double2 v) { return make_double2(wsum(v.x), wsum(v.y)); }
 
+// Column s of Q completed from the unit vector e_k whose residual
+// 1 - sum_{i<s} |Q[k][i]|^2 against the columns taken is largest (first k on
+// ties), orthogonalized twice and normalized; zero when no unit vector has a
+// residual (Q already spans the rows).  Used past the numerical rank of M, so
+// that Q keeps orthonormal columns there (as a Householder QR's Q does)
+// instead of normalized rounding noise, which has no room left when M's rows
+// span fewer dimensions than r (stacked coefficient blocks with zero rows).
+__device__ void qr_complete(double2* Q, int rows, int r, int s, int lane)
+{
+    double bres = -1.0;
+    int bk = rows;
+    for (int k = lane; k < rows; k += 32) {
+        double sq = 0.0;
+        for (int i = 0; i < s; ++i) {
+            const double2 v = Q[(size_t)k * r + i];
+            sq += v.x * v.x + v.y * v.y;
+        }
+        const double res = 1.0 - sq;
+        if (res > bres) {
+            bres = res;
+            bk = k;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ores = __shfl_xor_sync(0xffffffffu, bres, o);
+        const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        if (ores > bres || (ores == bres && ok < bk)) {
+            bres = ores;
+            bk = ok;
+        }
+    }
+    if (!(bres > 1e-3) || bk >= rows) {
+        for (int q = lane; q < rows; q += 32) Q[(size_t)q * r + s] = dz();
+        __syncwarp();
+        return;
+    }
+    // v = e_bk - Q (Q^H e_bk), then a second projection and the norm
+    for (int q = lane; q < rows; q += 32) {
+        double2 v = make_double2(q == bk ? 1.0 : 0.0, 0.0);
+        for (int i = 0; i < s; ++i) {
+            const double2 d = dmul(Q[(size_t)q * r + i], make_double2(Q[(size_t)bk * r + i].x, -Q[(size_t)bk * r + i].y));
+            v.x -= d.x;
+            v.y -= d.y;
+        }
+        Q[(size_t)q * r + s] = v;
+    }
+    __syncwarp();
+    for (int i = 0; i < s; ++i) {
+        double2 cf = dz();
+        for (int q = lane; q < rows; q += 32) {
+            const double2 d = dcmul(Q[(size_t)q * r + i], Q[(size_t)q * r + s]);
+            cf.x += d.x;
+            cf.y += d.y;
+        }
+        cf = wsum2(cf);
+        __syncwarp();
+        for (int q = lane; q < rows; q += 32) {
+            const double2 d = dmul(cf, Q[(size_t)q * r + i]);
+            Q[(size_t)q * r + s].x -= d.x;
+            Q[(size_t)q * r + s].y -= d.y;
+        }
+        __syncwarp();
+    }
+    double nn = 0.0;
+    for (int q = lane; q < rows; q += 32) {
+        const double2 v = Q[(size_t)q * r + s];
+        nn += v.x * v.x + v.y * v.y;
+    }
+    nn = wsum(nn);
+    const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    for (int q = lane; q < rows; q += 32) {
+        const double2 v = Q[(size_t)q * r + s];
+        Q[(size_t)q * r + s] = make_double2(v.x * inv, v.y * inv);
+    }
+    __syncwarp();
+}
+
 // First r columns of Q of the column-pivoted QR of M (rows x C, row-major,
-// overwritten by residuals) into Q (rows x r, row-major); columns past the
-// numerical rank or past min(rows, C) are zero.
+// overwritten by residuals) into Q (rows x r, row-major).  Past the numerical
+// rank of M (a remaining column norm below 1e-13 of the largest initial one)
+// the columns are orthonormal completions (qr_complete); past min(rows, r)
+// they are zero.
 __device__ void warp_qrcp(double2* M, int rows, int C, int r, double2* Q, int lane)
 {
     uint32_t used = 0;
+    double nmax0 = 0.0;
+    for (int c = 0; c < C; ++c) {
+        double nn = 0.0;
+        for (int q = lane; q < rows; q += 32) {
+            const double2 v = M[(size_t)q * C + c];
+            nn += v.x * v.x + v.y * v.y;
+        }
+        nmax0 = fmax(nmax0, wsum(nn));
+    }
     for (int s = 0; s < r; ++s) {
         int best = -1;
         double bestn = 0.0;
@@ -73,9 +162,13 @@ __device__ void warp_qrcp(double2* M, int rows, int C, int r, double2* Q, int la
                 }
             }
         }
-        if (best < 0) {
-            for (int q = lane; q < rows; q += 32) Q[(size_t)q * r + s] = dz();
-            __syncwarp();
+        if (best < 0 || !(bestn > 1e-26 * nmax0)) {
+            if (s < rows) {
+                qr_complete(Q, rows, r, s, lane);
+            } else {
+                for (int q = lane; q < rows; q += 32) Q[(size_t)q * r + s] = dz();
+                __syncwarp();
+            }
             continue;
         }
         used |= 1u << best;

@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("n,L,b,r,R,p", [(256, 4, 16, 4, 4, 5), (1024, 6, 16, 6, 3, 5), (512, 5, 16, 8, 8, 5),
-                                         (64, 0, 64, 4, 4, 3), (128, 1, 64, 5, 5, 2), (4096, 8, 16, 6, 6, 5)])
+                                         (64, 0, 64, 4, 4, 3), (128, 1, 64, 5, 5, 2), (4096, 8, 16, 6, 6, 5),
+                                         (1024, 8, 4, 12, 10, 5), (256, 6, 4, 12, 12, 3)])
 def test_lr2bf_parity(n, L, b, r, R, p):
     rng = synth.SplitMix64(101 + n + R)
     A = rng.cnormal(n * R).reshape(n, R)
@@ -36,7 +37,10 @@ def test_lr2bf_parity(n, L, b, r, R, p):
     assert rel_dev(xg, t) <= 1e-10                      # reproduces A B^T
     xo = oracle.eval_entries(n, L, b, r, Xo, i, j)
     assert rel_dev(xg, xo) <= 1e-10
-    if R == r:
+    if R == r and b >= r:
+        # full-rank pivots everywhere: the factors are unique (a rank-deficient
+        # step completes Q with arbitrary orthonormal columns, chosen
+        # differently by LAPACK and by the warp QR)
         assert rel_dev(Xg, Xo) <= 1e-8
 
 

@@ -190,7 +190,8 @@ def test_adam_without_moments_is_sign_descent():
 # ------------------------------------------------------------------ Alg. 2
 
 @pytest.mark.parametrize("n,L,b,r,R,p", [(64, 2, 16, 4, 4, 5), (128, 3, 16, 4, 3, 5), (256, 4, 16, 6, 6, 3),
-                                         (32, 0, 32, 3, 3, 2), (64, 1, 32, 4, 4, 5), (512, 5, 16, 8, 8, 5)])
+                                         (32, 0, 32, 3, 3, 2), (64, 1, 32, 4, 4, 5), (512, 5, 16, 8, 8, 5),
+                                         (64, 4, 4, 12, 10, 5), (128, 5, 4, 12, 12, 5)])
 def test_alg2_reproduces_exact_low_rank(n, L, b, r, R, p):
     rng = synth.SplitMix64(7 + n + R)
     A = rng.cnormal(n * R).reshape(n, R)
@@ -204,13 +205,19 @@ def test_alg2_reproduces_exact_low_rank(n, L, b, r, R, p):
     assert np.abs(x - T).max() <= 1e-12 * np.abs(T).max()
     # the outer factors are orthonormal bases of the leaf blocks (z1 only
     # when the middle level is not z1 itself)
+    # b >= r: the leaf blocks of z1 and zL are orthonormal bases (z1 only when
+    # the middle level is not z1 itself); b < r: their b columns are, and the
+    # rest are zero
     z1, _, zL = split_packed(X, n, L, b, r)
+    k = min(b, r)
+    eye = np.zeros((r, r))
+    eye[:k, :k] = np.eye(k)
     for q in range(n // b):
         blk = zL[q * b:(q + 1) * b]
-        np.testing.assert_allclose(blk.conj().T @ blk, np.eye(r), atol=1e-12)
+        np.testing.assert_allclose(blk.conj().T @ blk, eye, atol=1e-12)
         if L >= 2:
             blk = z1[q * b:(q + 1) * b]
-            np.testing.assert_allclose(blk.conj().T @ blk, np.eye(r), atol=1e-12)
+            np.testing.assert_allclose(blk.conj().T @ blk, eye, atol=1e-12)
 
 
 def test_alg2_gaussian_layout_matches_synth():
