@@ -657,13 +657,23 @@ def run_first_order(bfc_mod, c, prob, hbm_peak, iters=3, nvec=64):
     prof = c.profile_read()
     c.profile(False)
     ms = sum(v[1] for v in prof.values())
-    fbytes = c.P * (8 if c.params.prec == bfc_mod.PREC_C64 else 16)
-    by = fbytes + 2 * prob.n * nvec * 16
+    vsz = 8 if c.params.prec == bfc_mod.PREC_C64 else 16
+    fbytes = c.P * vsz
+    # the level-by-level contraction streams its intermediates: per vector,
+    # the leaf writes n/b r-vectors, every middle level reads two children and
+    # writes one r-vector per slice, the root reads two per leaf block
+    r, L, S, nb = prob.r, prob.L, 1 << (prob.L + 1), prob.n // prob.b
+    inter = nvec * r * vsz * (nb + (L - 1) * 3 * S + 2 * S + 2 * nb)
+    by = fbytes + 2 * prob.n * nvec * 16 + inter
     out["matvec"] = {"nvec": nvec, "kernel_ms": ms, "vectors_per_s": nvec / (ms * 1e-3),
                      "kernels_ms": {k: round(v[1], 4) for k, v in prof.items()},
                      "roofline": {"bound": "hbm", "bytes": by, "achieved": by / (ms * 1e-3) / 1e9,
                                   "peak": hbm_peak, "unit": "GB/s", "frac": by / (ms * 1e-3) / 1e9 / hbm_peak,
-                                  "per_unit": "all factors once (compute type) + 16 B per vector entry in and out"}}
+                                  "per_unit": "all factors once (compute type) + 16 B per vector entry in and out + "
+                                              "the level intermediates (r values per slice and vector: the leaf "
+                                              "writes n/b, each middle level reads 2 S and writes S, the root "
+                                              "reads 2 n/b)",
+                                  "flop": 8 * nvec * (prob.n * r + L * S * r * r + prob.n * r)}}
     return out
 
 

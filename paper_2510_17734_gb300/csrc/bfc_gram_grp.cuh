@@ -130,9 +130,10 @@ k_group_sums(const typename cvec<T>::type* __restrict__ H, const typename cvec<T
     const int g = gb0 + (int)threadIdx.x / R, a = (int)threadIdx.x % R;
     if (g >= gb1) return;
     const int e0 = gstart[g], e1 = gstart[g + 1];
-    // generic pointers into shared or global memory, indexed by the entry
-    const V* ub = staged ? su - (size_t)E0 * R : Uv;
-    const V* tb = staged ? st - E0 : tv;
+    // the block's entries in shared memory (staged) or global memory, indexed
+    // from the block's first entry E0
+    const V* ub = staged ? su : Uv + (size_t)E0 * R;
+    const V* tb = staged ? st : tv + E0;
     V* o = out + (size_t)g * RS;
     o[a] = Sv[(size_t)e0 * R + a];
     V ms[R], vs;
@@ -151,13 +152,13 @@ k_group_sums(const typename cvec<T>::type* __restrict__ H, const typename cvec<T
         const int ee = min(eb + 16, e1);
         for (int e = eb; e < ee; ++e) {
             V u[R];
-            const V* row = ub + (size_t)e * R;
+            const V* row = ub + (size_t)(e - E0) * R;
 #pragma unroll
             for (int q = 0; q < R; ++q) u[q] = row[q];
             const V ua = row[a];   // one more load instead of a select chain
 #pragma unroll
             for (int q = 0; q < R; ++q) cmacc(mp[q], ua, u[q]);
-            cmacc(vp, ua, tb[e]);
+            cmacc(vp, ua, tb[e - E0]);
         }
         if constexpr (sizeof(T) == 4) {
 #pragma unroll

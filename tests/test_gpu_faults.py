@@ -95,3 +95,24 @@ def test_inject_rejects_unknown_kind(cfg1):
     with _make(p, bfc.PREC_FP64) as c:
         with pytest.raises(bfc.BfcError, match="EINVAL"):
             bfc.bfc_inject_fault(c.ctx, 3)
+
+
+def test_batch_launch_reports_timeout_and_recovers():
+    """An expired bounded wait inside the one-launch batch stops that
+    problem's loop on the device; the batch returns BFC_ETIMEOUT and, with
+    injection off, the same contexts complete normally."""
+    probs = synth.batch_problems(count=2, n_choices=(1024,))
+    cs = [bfc.Completion(p.n, p.L, p.b, p.r, p.lam, p.i, p.j, p.t, p.it, p.jt, p.tt, prec=bfc.PREC_C64,
+                         max_sweeps=4, tol=1e-12, seed=5 + q, init_kind=1, lr_sweeps=5, gram_impl=bfc.GRAM_CUDA)
+          for q, p in enumerate(probs)]
+    try:
+        bfc.bfc_inject_fault(cs[1].ctx, 1)
+        with pytest.raises(bfc.BfcError, match="ETIMEOUT"):
+            bfc.batch_complete(cs)
+        bfc.bfc_inject_fault(cs[1].ctx, 0)
+        last = bfc.batch_complete(cs)
+        assert all(st["sweep"] > 0 and np.isfinite(st["train_rel_err"]) for st in last)
+        assert all(st["batch_launches"] == 1 for st in last)
+    finally:
+        for c in cs:
+            c.close()

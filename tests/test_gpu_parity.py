@@ -454,7 +454,7 @@ def test_invalid_inputs_rejected():
     with pytest.raises(bfc.BfcError, match="EINVAL"):
         bfc.Completion(n, L, 8, r, 1e-6, i, j, t)             # n != b 2^L
     with pytest.raises(bfc.BfcError, match="EINVAL"):
-        bfc.Completion(n, L, b, 11, 1e-6, i, j, t)            # rank too large
+        bfc.Completion(n, L, b, 13, 1e-6, i, j, t)            # rank too large (max 12)
     with pytest.raises(bfc.BfcError, match="EINVAL"):
         bfc.Completion(n, L, b, r, -1.0, i, j, t)             # lambda < 0
     bad = i.copy()
