@@ -244,7 +244,9 @@ static bfc_status build(Ctx* c, const Inputs& in)
         BFC_TRY(dalloc(c, (void**)&perm[l], N * 4, "perm"));
         BFC_TRY(tmp((void**)&pos[l], N * 4, "pos"));
         BFC_TRY(dalloc(c, (void**)&c->seg[l], (K + 1) * 4, "segments"));
-        BFC_TRY(dalloc(c, &c->tval[l], N * c->vsz, "level values"));
+        // + 16 bytes: the tensor-core Gram's bulk copies round their end up to
+        // a 16-byte boundary
+        BFC_TRY(dalloc(c, &c->tval[l], N * c->vsz + 16, "level values"));
         // middle levels: inside a slice, entries of one row (levels m with
         // 2m <= L+1, where a slice's block has fewer rows than columns) or of
         // one column are contiguous; they share h_m (resp. w_m)
@@ -322,9 +324,9 @@ static bfc_status build(Ctx* c, const Inputs& in)
     if (hflag & 4) return fail(c, BFC_EINVAL, "duplicate (i, j) pair in the training set");
 
     // environments
-    BFC_TRY(dalloc(c, &c->W, (size_t)(L + 1) * N * r * c->vsz, "right environments"));
+    BFC_TRY(dalloc(c, &c->W, (size_t)(L + 1) * N * r * c->vsz + 16, "right environments"));
     for (int q = 0; q < 2; ++q) {
-        BFC_TRY(dalloc(c, &c->H[q], (size_t)N * r * c->vsz, "left environments"));
+        BFC_TRY(dalloc(c, &c->H[q], (size_t)N * r * c->vsz + 16, "left environments"));
         BFC_TRY(dalloc(c, &c->Rres[q], (size_t)N * c->vsz, "residuals"));
     }
     // factors: one allocation, FP64 master [z1 | Z | zL]

@@ -63,11 +63,20 @@ struct TcGram {
     static constexpr int SMALL_COL = 384;         // per-slice cross-term accumulator
     static constexpr int TMEM_COLS = 512;
     static constexpr int NBUILD = 8;              // builder / fold warps: 2 per TMEM lane quadrant
-    static constexpr int NTH = 32 * (NBUILD + 1); // + the MMA warp
+    static constexpr int NTH = 32 * (NBUILD + 2); // + the MMA warp + the input-loader warp
     static constexpr int SCR_LD = 81;             // record scratch row stride (floats)
     static constexpr int SCR = 128 * SCR_LD * 4;  // record scratch: 128 lanes x 80 columns
     static constexpr int SEGC = 1024;             // cached (start, end) of this CTA's first slices
-    static constexpr size_t SMEM = 1024 + 2 * (size_t)STAGE + SCR + 8 * (size_t)SEGC + 128;
+    static constexpr int NBARS = 19;              // 11 pipeline barriers + 2 x NIN input-ring barriers
+    static constexpr int TAIL = 256;              // barriers, TMEM slot, abort flag
+    // input ring: the h and w rows and the t values of a chunk, copied in by
+    // bulk copies from 16-byte-aligned starts (up to 15 leading bytes and a
+    // rounded-up end: 32 bytes of slack per array)
+    static constexpr int NIN = 4;
+    static constexpr int HB = CE * 8 * 8 + 32;    // rows of up to 8 complex64 values
+    static constexpr int TB = CE * 8 + 32;
+    static constexpr int INSTG = 2 * HB + TB;     // one ring stage (a multiple of 16 bytes)
+    static constexpr size_t SMEM = 1024 + 2 * (size_t)STAGE + SCR + 8 * (size_t)SEGC + TAIL + (size_t)NIN * INSTG;
     static constexpr uint32_t WAIT_LIMIT = 1u << 22;
 };
 
@@ -220,8 +229,11 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
     uint64_t* accfull = bars + 4;     // [NBIG]  MMA commit -> builders (chunk accumulated)
     uint64_t* accempty = bars + 7;    // [NBIG]  builders' fold -> MMA warp (count NBUILD)
     uint64_t* sempty = bars + 10;     // [1]     builders read the cross terms -> MMA warp (count NBUILD)
-    uint32_t* tmem_slot = (uint32_t*)(bars + 11);
+    uint64_t* infull = bars + 11;     // [NIN]   bulk copies of a chunk's inputs landed (loader, tx bytes)
+    uint64_t* inempty = bars + 15;    // [NIN]   builders read the stage (count NBUILD)
+    uint32_t* tmem_slot = (uint32_t*)(bars + TcGram::NBARS);
     volatile int* abort_s = (volatile int*)(tmem_slot + 1);
+    unsigned char* inring = (unsigned char*)bars + TcGram::TAIL;           // [NIN][INSTG]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -238,8 +250,10 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
         segc[i] = make_int2(seg[k], seg[k + 1]);
     }
     if (tid == 0) {
-        for (int i = 0; i < 11; ++i) {
-            const uint32_t cnt = (i < 2 || i >= 7) ? (uint32_t)TcGram::NBUILD : 1u;
+        for (int i = 0; i < TcGram::NBARS; ++i) {
+            // full, accempty, sempty, inempty: one arrival per builder warp;
+            // empty, accfull (MMA commits), infull (loader): one
+            const uint32_t cnt = (i < 2 || (i >= 7 && i < 11) || i >= 15) ? (uint32_t)TcGram::NBUILD : 1u;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem_u32(&bars[i])), "r"(cnt));
         }
         *abort_s = 0;
@@ -287,7 +301,60 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
         return first_of(c.k + gridDim.x, c.sl + 1);
     };
 
-    if (warp == TcGram::NBUILD) {
+    // one ring stage: h rows at 0, w rows at HB, t values at 2 HB; the byte
+    // offsets of a chunk's first row inside each (the copies start at the
+    // 16-byte boundary at or before it)
+    auto in_off = [&](const void* base_ptr, int64_t first, int bytes_per) {
+        return (int)(((uintptr_t)base_ptr + (uintptr_t)first * bytes_per) & 15u);
+    };
+    if (warp == TcGram::NBUILD + 1) {
+        // ------------------------------------------------------ loader warp
+        // Bulk copies of every chunk's h rows, w rows and t values into the
+        // input ring, NIN chunks ahead of the builders.
+        if (lane == 0) {
+            int g = 0;
+            for (TcChunk c = first_of(blockIdx.x, 0); c.valid; c = advance(c), ++g) {
+                const int st = g % TcGram::NIN;
+                if (g >= TcGram::NIN)
+                    tc_wait(tc_smem_u32(&inempty[st]), (uint32_t)((g / TcGram::NIN - 1) & 1), abort_s, err);
+                if (*abort_s) break;
+                unsigned char* dst = inring + (size_t)st * TcGram::INSTG;
+                const int cnt = c.cnt();
+                const void* srcs[3] = {H, Wm, tv};
+                const int bper[3] = {R * 8, R * 8, 8};
+                const int doff[3] = {0, TcGram::HB, 2 * TcGram::HB};
+                uint32_t sz[3];
+                uint32_t total = 0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const uintptr_t b0 = (uintptr_t)srcs[a] + (uintptr_t)c.base * bper[a];
+                    const uintptr_t b1 = b0 + (uintptr_t)cnt * bper[a];
+                    const uintptr_t a0 = b0 & ~(uintptr_t)15, a1 = (b1 + 15) & ~(uintptr_t)15;
+                    sz[a] = (uint32_t)(a1 - a0);
+                    total += sz[a];
+                }
+                asm volatile("{\n.reg .b64 stt;\nmbarrier.arrive.expect_tx.shared::cta.b64 stt, [%0], %1;\n}\n"
+                             ::"r"(tc_smem_u32(&infull[st])), "r"(total) : "memory");
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const uintptr_t b0 = (uintptr_t)srcs[a] + (uintptr_t)c.base * bper[a];
+                    const uintptr_t a0 = b0 & ~(uintptr_t)15;
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 ::"r"(tc_smem_u32(dst + doff[a])), "l"((const void*)a0), "r"(sz[a]),
+                                   "r"(tc_smem_u32(&infull[st]))
+                                 : "memory");
+                }
+            }
+            // copies given up on after an abort may still land: wait for the
+            // last phase issued on every stage (bounded) before the CTA exits
+            for (int st = 0; st < TcGram::NIN && st < g; ++st) {
+                const int last = st + ((g - 1 - st) / TcGram::NIN) * TcGram::NIN;
+                for (uint32_t it = 0; it < TcGram::WAIT_LIMIT; ++it)
+                    if (tc_try_wait(tc_smem_u32(&infull[st]), (uint32_t)((last / TcGram::NIN) & 1))) break;
+            }
+        }
+        __syncwarp();
+    } else if (warp == TcGram::NBUILD) {
         // ------------------------------------------------------------ MMA warp
         // The first chunk of a slice puts all three products into its hi*hi
         // accumulator; later chunks send the cross terms to the slice's
@@ -447,50 +514,58 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
         const uint32_t t_off = (uint32_t)(r8 * 128 + ((((lane >> 2) ^ r8)) << 4) + (lane & 3) * 4);
         const int e = lane;
 
-        // the h_p, w_c (and t) this thread needs for chunk c, in registers
-        // (rank 8: p = j and c = r8, so one w and the whole h)
+        // the h_p, w_c (and t) this thread needs for chunk c, from the input
+        // ring stage of the chunk (rank 8: p = j and c = r8, so one w and the
+        // whole h); the stage is released to the loader once read
         constexpr int NW = R == 8 ? 1 : 8;
         struct Vals { float2 h[8], w[NW], t; };
-        auto load = [&](const TcChunk& c, Vals& vl) {
+        auto load = [&](const TcChunk& c, int gc, Vals& vl) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) vl.h[j] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < NW; ++j) vl.w[j] = make_float2(0.f, 0.f);
             vl.t = make_float2(0.f, 0.f);
-            if (!c.valid || e >= c.cnt()) return;
-            const size_t ent = (size_t)(c.base + e);
-            if (R == 8) {
-                const float4* hp = (const float4*)(H + ent * R);
+            const int st = gc % TcGram::NIN;
+            tc_wait(tc_smem_u32(&infull[st]), (uint32_t)((gc / TcGram::NIN) & 1), abort_s, err);
+            const unsigned char* sb = inring + (size_t)st * TcGram::INSTG;
+            const float2* hs = (const float2*)(sb + in_off(H, c.base, R * 8));
+            const float2* ws = (const float2*)(sb + TcGram::HB + in_off(Wm, c.base, R * 8));
+            const float2* ts = (const float2*)(sb + 2 * TcGram::HB + in_off(tv, c.base, 8));
+            if (e < c.cnt()) {
+                if (R == 8) {
+                    const float4* hp = (const float4*)(hs + e * R);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float4 h2 = __ldg(hp + j);
-                    vl.h[2 * j] = make_float2(h2.x, h2.y);
-                    vl.h[2 * j + 1] = make_float2(h2.z, h2.w);
-                }
-                vl.w[0] = __ldg(Wm + ent * R + r8);
-            } else {
+                    for (int j = 0; j < 4; ++j) {
+                        const float4 h2 = hp[j];
+                        vl.h[2 * j] = make_float2(h2.x, h2.y);
+                        vl.h[2 * j + 1] = make_float2(h2.z, h2.w);
+                    }
+                    vl.w[0] = ws[e * R + r8];
+                } else {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int q = r8 + 8 * j;
-                    if (q < D) {
-                        vl.h[j] = __ldg(H + ent * R + q / R);
-                        vl.w[j % NW] = __ldg(Wm + ent * R + q % R);
+                    for (int j = 0; j < 8; ++j) {
+                        const int q = r8 + 8 * j;
+                        if (q < D) {
+                            vl.h[j] = hs[e * R + q / R];
+                            vl.w[j % NW] = ws[e * R + q % R];
+                        }
                     }
                 }
+                if (warp == 0) vl.t = ts[e];
             }
-            if (warp == 0) vl.t = __ldg(tv + ent);
+            __syncwarp();
+            if (lane == 0) tc_arrive(tc_smem_u32(&inempty[st]));
         };
 
         TcChunk cur = first_of(blockIdx.x, 0);
         TcFold f1, f2;   // chunks g-1 and g-2, folded two chunks late
         f1.valid = false;
         f2.valid = false;
-        Vals vc, vn;
-        load(cur, vc);
+        Vals vc;
         int g = 0;
         while (cur.valid) {
             const TcChunk nxt = advance(cur);
-            load(nxt, vn);   // the next chunk's values are in flight during this chunk
+            load(cur, g, vc);
             const int b = g & 1;
             if (g >= 2) tc_wait(tc_smem_u32(&empty[b]), (uint32_t)(((g - 2) >> 1) & 1), abort_s, err);
             unsigned char* st = ops + b * TcGram::STAGE;
@@ -533,7 +608,6 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             f1.last = cur.last();
             f1.multi = cur.idx > 0;
             cur = nxt;
-            vc = vn;
             ++g;
         }
         if (f2.valid) fold(f2);
