@@ -54,7 +54,7 @@ METRIC = "ALS sweep entries/s (n=65536 precision form)"
 UNIT = "entries/s"
 WORKLOAD = ("n=65536 L=12 b=16 r=8, exp(i w rho)/rho line-to-line kernel, w=pi n/16, h=1.5, "
             "|Omega|=4 n log2 n (3774874 train / 419430 test), lambda=1e-7")
-TC_FLOPS_PER_ENTRY = 2 * 3 * 128 * 80 * 2   # flop, 2 positions x M 128 x N 80 x 3 products
+TC_FLOPS_PER_ENTRY = 2 * 3 * 128 * 144   # flop, one contraction position x M 128 x N 144 x 3 products
 # DRAM counters of one k_mid_gram_tc launch (ncu, n = 32768, L = 11: 1,769,472
 # entries, 4096 slices), valid for the kernel source with this sha256 prefix
 TC_GRAM_TRAFFIC = {"source": "paper_2510_17734_gb300/csrc/bfc_gram_tc.cuh", "sha": "ee52a82b4be1f55c",
@@ -287,9 +287,9 @@ def gram_rooflines(prob, prof, n_sweeps, c64, tc_levels, grouped, peaks, fp32_me
                         "per_unit": f"{als_flops_per_entry(r)} flop per entry (Hermitian Gram + right-hand side)",
                         "peak_source": "MEASURED_PEAKS bf16_tflops_sustained x 1.1/2.25 (of measured)",
                         "executed_tflops": executed, "executed_frac": executed / peak,
-                        "executed_note": "issued MMA flops: 128 x 80 real embedding of the complex Gram "
-                                         "(Re and Im, full square, 2 contraction positions per entry) x 3 TF32 "
-                                         "split products = 122880 flop per entry",
+                        "executed_note": "issued MMA flops: 128 x 144 real embedding of the complex Gram "
+                                         "(uu, uv, vu, vv full squares and the right-hand side, one contraction "
+                                         "position per entry) x 3 TF32 split products = 110592 flop per entry",
                         "fp32_peak": fp32_meas, "fp32_frac": a / fp32_meas})
         else:
             peak = fp32_meas if c64 else fp64_meas

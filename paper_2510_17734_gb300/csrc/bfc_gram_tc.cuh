@@ -6,46 +6,52 @@
 // read as a linear function of one slice).  Same output record as the
 // CUDA-core k_mid_gram: K packed lower-triangular, then y.
 //
-// Real form of the complex sums.  Write a = u + i v and give every entry two
-// positions on the contraction axis (part 0, part 1).  With the rows
-//     P_q = (u_q, v_q),   Q_p = (v_p, -u_p),   T = (Re t, Im t),
-//     Re K[p][q] = P_p . P_q,   Im K[p][q] = -(Q_p . P_q),
-//     Re y[p]    = P_p . T,     Im y[p]    = -(Q_p . T).
-// Shared memory holds the rows in the order Q (64 rows) | P (64) | T (1) |
-// zeros (15), so one MMA with A = rows 0..127 (M = 128) and B = rows
-// 64..143 (N = 80) produces all of them: D[p][q] = -Im K, D[64+p][q] = Re K,
-// column 64 the two parts of y.
+// Real form of the complex sums.  Write a = u + i v.  Then
+//     Re K[p][q] = UU[p][q] + VV[p][q],   Im K[p][q] = UV[p][q] - VU[p][q],
+//     Re y[p] = U.Re t + V.Im t,           Im y[p] = U.Im t - V.Re t,
+// with UU = sum u u^T, UV = sum u v^T and so on.  Shared memory holds one
+// row per real feature, u_q and v_q (128 rows), then Re t, Im t and zero
+// rows up to 144, every entry one position of the contraction axis.  One
+// MMA with A = rows 0..127 (M = 128) and B = rows 0..143 of the same tiles
+// (N = 144) yields all of UU, UV, VU, VV and the four y products.  The rows
+// are ordered so that u_p and v_p sit 16 TMEM lanes apart in one warp's
+// quadrant (u_p at 32 (p / 16) + p % 16, v_p 16 rows later): at the fold a
+// lane pairs its own columns with its partner's by one shuffle per column
+// (the u lane keeps Re K, the v lane Im K).
 //
 // Precision: every operand is split into TF32 parts, x = hi + lo, and the
 // product is taken as hi*hi + (lo*hi + hi*lo) (three MMAs), which keeps it to
 // about FP32 accuracy.  The tensor core's FP32 accumulation into D
 // truncates: every update loses about 2^-24 |D| towards zero, a bias that
 // grows with the number of updates into one accumulator (measured on the
-// diagonal of K: -1.2e-6 relative with all three products of two chunks in
-// one accumulator, enough to stall ALS near 1e-3 test error).  So every
-// chunk gets its own hi*hi accumulator (8 updates), folded into per-thread
-// Kahan sums, while the cross terms, 2^-11 smaller, run over the whole
-// slice in one accumulator (bias -4e-7; the sweeps follow the FP64
-// trajectory).  The first chunk of a slice puts all three products into its
-// hi*hi accumulator, so the cross-term accumulator of the previous slice can
-// still be read while the next slice starts.
+// diagonal of K: -1.2e-6 relative with all three products of two 32-entry
+// chunks in one accumulator, enough to stall ALS near 1e-3 test error).  So
+// every chunk of 64 entries gets its own hi*hi accumulator (at most 8
+// updates), folded into per-thread Kahan sums, while the cross terms, 2^-11
+// smaller, run over the whole slice in one accumulator.  The first chunk of
+// a slice puts all three products into its hi*hi accumulator, so the
+// cross-term accumulator of the previous slice can still be read while the
+// next slice starts.  A chunk issues only the k-steps (8 entries each) that
+// hold entries.
 //
-// Roles (one persistent CTA of 9 warps per SM; slices round-robin):
-//   warps 0..7   load h, w, t of chunk g+1 into registers, build the TF32
-//                operand rows of chunk g in operand stage g&1, signal
-//                full[g&1]; then fold the hi*hi accumulator of chunk g-2
-//                (two chunks late, so it is complete) into the Kahan sums
-//                (tcgen05.ld, lower triangle only), signal accempty, and at
-//                the end of a slice add its cross terms, signal sempty and
-//                write the record (through a shared-memory scratch, so the
-//                global stores are coalesced)
+// Roles (one persistent CTA of 10 warps per SM; slices round-robin):
+//   warp 9       loader: bulk copies of every chunk's h rows, w rows and t
+//                values into a 4-stage input ring
+//   warps 0..7   build the TF32 operand rows of chunk g from the ring in
+//                operand stage g&1, signal full[g&1]; then fold the hi*hi
+//                accumulator of chunk g-1 into the Kahan sums (tcgen05.ld,
+//                the column blocks of the lower triangle only), signal
+//                accempty, and at the end of a slice add its cross terms,
+//                signal sempty and write the record (through a shared-memory
+//                copy of the packed record, so the global stores are
+//                coalesced)
 //   warp 8       waits full[s] (and accempty / sempty when it reuses an
-//                accumulator), issues the 24 MMAs of the chunk, commits to
+//                accumulator), issues the MMAs of the chunk, commits to
 //                empty[s] and accfull
 // Every mbarrier wait is bounded; on expiry the kernel raises *err, after
 // which all waits return at once (the work still runs to its end with the
 // same control flow in every warp, results undefined), then waits (bounded)
-// for its MMAs, frees its TMEM and returns.
+// for its MMAs and copies, frees its TMEM and returns.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -54,31 +60,35 @@
 namespace bfc {
 
 struct TcGram {
-    static constexpr int CE = 32;                 // entries per chunk (one K block of 32 TF32)
-    static constexpr int ROWS = 144;              // Q 0..63 | P 64..127 | T 128 | zeros
+    static constexpr int CE = 64;                 // entries per chunk: two K blocks of 32 TF32
+    static constexpr int ROWS = 144;              // u / v feature rows 0..127 | Re t 128 | Im t 129 | zeros
     static constexpr int KB = ROWS * 128;         // one K block: 144 rows x 128 B (SW128 atoms)
-    static constexpr int STAGE = 4 * KB;          // [part][hi/lo] K blocks
-    static constexpr int NCOL = 80;               // accumulator columns (N)
-    static constexpr int NBIG = 3;                // per-chunk hi*hi accumulators at TMEM columns 0, 128, 256
-    static constexpr int SMALL_COL = 384;         // per-slice cross-term accumulator
+    static constexpr int STAGE = 4 * KB;          // [entry block][hi/lo] K blocks
+    static constexpr int NCOL = 144;              // accumulator columns (N)
+    static constexpr int NBIG = 2;                // per-chunk hi*hi accumulators at TMEM columns 0, 160
+    static constexpr int ACC_STRIDE = 160;
+    static constexpr int SMALL_COL = 320;         // per-slice cross-term accumulator
     static constexpr int TMEM_COLS = 512;
     static constexpr int NBUILD = 8;              // builder / fold warps: 2 per TMEM lane quadrant
     static constexpr int NTH = 32 * (NBUILD + 2); // + the MMA warp + the input-loader warp
-    static constexpr int SCR_LD = 81;             // record scratch row stride (floats)
-    static constexpr int SCR = 128 * SCR_LD * 4;  // record scratch: 128 lanes x 80 columns
+    static constexpr int RECB = (64 * 65 / 2 + 64) * 8;  // packed record copy (rank 8; a multiple of 16 bytes)
     static constexpr int SEGC = 1024;             // cached (start, end) of this CTA's first slices
-    static constexpr int NBARS = 19;              // 11 pipeline barriers + 2 x NIN input-ring barriers
+    static constexpr int NIN = 4;
+    static constexpr int NBARS = 9 + 2 * NIN;     // 9 pipeline barriers + 2 x NIN input-ring barriers
     static constexpr int TAIL = 256;              // barriers, TMEM slot, abort flag
     // input ring: the h and w rows and the t values of a chunk, copied in by
     // bulk copies from 16-byte-aligned starts (up to 15 leading bytes and a
     // rounded-up end: 32 bytes of slack per array)
-    static constexpr int NIN = 4;
     static constexpr int HB = CE * 8 * 8 + 32;    // rows of up to 8 complex64 values
     static constexpr int TB = CE * 8 + 32;
     static constexpr int INSTG = 2 * HB + TB;     // one ring stage (a multiple of 16 bytes)
-    static constexpr size_t SMEM = 1024 + 2 * (size_t)STAGE + SCR + 8 * (size_t)SEGC + TAIL + (size_t)NIN * INSTG;
+    static constexpr size_t SMEM = 1024 + 2 * (size_t)STAGE + RECB + 8 * (size_t)SEGC + TAIL + (size_t)NIN * INSTG;
     static constexpr uint32_t WAIT_LIMIT = 1u << 22;
 };
+static_assert(TcGram::NBARS * 8 + 8 <= TcGram::TAIL, "barrier area");
+static_assert(TcGram::RECB % 16 == 0 && TcGram::INSTG % 16 == 0 && TcGram::HB % 16 == 0, "16-byte layout");
+static_assert(TcGram::SMALL_COL + TcGram::NCOL <= TcGram::TMEM_COLS &&
+              TcGram::ACC_STRIDE * (TcGram::NBIG - 1) + TcGram::NCOL <= TcGram::SMALL_COL, "TMEM columns");
 
 __device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -152,20 +162,12 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v)
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
-__device__ __forceinline__ void tc_ld1(uint32_t taddr, float* v)
+__device__ __forceinline__ void tc_ld2(uint32_t taddr, float* v)
 {
-    uint32_t r;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
-    v[0] = __uint_as_float(r);
-}
-__device__ __forceinline__ void tc_ld4(uint32_t taddr, float* v)
-{
-    uint32_t r[4];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(taddr));
-#pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
+    uint32_t r[2];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+    v[0] = __uint_as_float(r[0]);
+    v[1] = __uint_as_float(r[1]);
 }
 
 // Packed pairs of FP32 values (the f32x2 arithmetic of sm_100 and later):
@@ -221,16 +223,16 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw_s = tc_smem_u32(smem_raw);
     unsigned char* ops = smem_raw + ((1024u - (raw_s & 1023u)) & 1023u);  // 2 operand stages
-    float* scr = (float*)(ops + 2 * TcGram::STAGE);                        // record scratch
-    int2* segc = (int2*)((unsigned char*)scr + TcGram::SCR);               // slice bounds cache
+    float* recs = (float*)(ops + 2 * TcGram::STAGE);                       // packed record copy
+    int2* segc = (int2*)((unsigned char*)recs + TcGram::RECB);             // slice bounds cache
     uint64_t* bars = (uint64_t*)(segc + TcGram::SEGC);
     uint64_t* full = bars;            // [2]     builders -> MMA warp (count NBUILD)
     uint64_t* empty = bars + 2;       // [2]     MMA commit -> builders (operand stage free)
     uint64_t* accfull = bars + 4;     // [NBIG]  MMA commit -> builders (chunk accumulated)
-    uint64_t* accempty = bars + 7;    // [NBIG]  builders' fold -> MMA warp (count NBUILD)
-    uint64_t* sempty = bars + 10;     // [1]     builders read the cross terms -> MMA warp (count NBUILD)
-    uint64_t* infull = bars + 11;     // [NIN]   bulk copies of a chunk's inputs landed (loader, tx bytes)
-    uint64_t* inempty = bars + 15;    // [NIN]   builders read the stage (count NBUILD)
+    uint64_t* accempty = bars + 6;    // [NBIG]  builders' fold -> MMA warp (count NBUILD)
+    uint64_t* sempty = bars + 8;      // [1]     builders read the cross terms -> MMA warp (count NBUILD)
+    uint64_t* infull = bars + 9;      // [NIN]   bulk copies of a chunk's inputs landed (loader, tx bytes)
+    uint64_t* inempty = bars + 9 + TcGram::NIN;   // [NIN] builders read the stage (count NBUILD)
     uint32_t* tmem_slot = (uint32_t*)(bars + TcGram::NBARS);
     volatile int* abort_s = (volatile int*)(tmem_slot + 1);
     unsigned char* inring = (unsigned char*)bars + TcGram::TAIL;           // [NIN][INSTG]
@@ -253,8 +255,9 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
         for (int i = 0; i < TcGram::NBARS; ++i) {
             // full, accempty, sempty, inempty: one arrival per builder warp;
             // empty, accfull (MMA commits), infull (loader): one
-            const uint32_t cnt = (i < 2 || (i >= 7 && i < 11) || i >= 15) ? (uint32_t)TcGram::NBUILD : 1u;
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem_u32(&bars[i])), "r"(cnt));
+            const bool per_builder = i < 2 || (i >= 6 && i < 9) || i >= 9 + TcGram::NIN;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
+                         ::"r"(tc_smem_u32(&bars[i])), "r"(per_builder ? (uint32_t)TcGram::NBUILD : 1u));
         }
         *abort_s = 0;
     }
@@ -373,26 +376,25 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
                     tc_wait(tc_smem_u32(&sempty[0]), (uint32_t)((c.sl - 1) & 1), abort_s, err);
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 if (*abort_s) continue;
-                const uint32_t d_big = tmem + (uint32_t)(bs * 128);
+                const uint32_t d_big = tmem + (uint32_t)(bs * TcGram::ACC_STRIDE);
                 const uint32_t d_small = tmem + (uint32_t)TcGram::SMALL_COL;
                 const bool head = c.idx == 0;
+                const int nks = (c.cnt() + 7) >> 3;   // k-steps of 8 entries that hold entries
                 const uint64_t sd = desc0 + (uint64_t)((b * TcGram::STAGE) >> 4);
 #pragma unroll
-                for (int part = 0; part < 2; ++part) {
-#pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint64_t a_hi = sd + (uint64_t)(((2 * part) * TcGram::KB + ks * 32) >> 4);
-                        const uint64_t a_lo = a_hi + (uint64_t)(TcGram::KB >> 4);
-                        const uint64_t b_hi = a_hi + (uint64_t)((64 * 128) >> 4);
-                        const uint64_t b_lo = a_lo + (uint64_t)((64 * 128) >> 4);
-                        const uint64_t A[3] = {a_lo, a_hi, a_hi};
-                        const uint64_t B[3] = {b_hi, b_lo, b_hi};
+                for (int s8 = 0; s8 < 8; ++s8) {
+                    if (s8 < nks) {
+                        const int kb = s8 >> 2, ks = s8 & 3;
+                        // A (rows 0..127) and B (rows 0..143) start at the same tile
+                        const uint64_t hi = sd + (uint64_t)(((2 * kb) * TcGram::KB + ks * 32) >> 4);
+                        const uint64_t lo = hi + (uint64_t)(TcGram::KB >> 4);
+                        const uint64_t A[3] = {lo, hi, hi};
+                        const uint64_t B[3] = {hi, lo, hi};
 #pragma unroll
                         for (int t = 0; t < 3; ++t) {
                             // t = 2 is hi*hi, t = 0, 1 the cross terms
                             const bool big = head || t == 2;
-                            const bool start = part == 0 && ks == 0 &&
-                                               (big ? t == (head ? 0 : 2) : (c.idx == 1 && t == 0));
+                            const bool start = s8 == 0 && (big ? t == (head ? 0 : 2) : (c.idx == 1 && t == 0));
                             asm volatile(
                                 "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
@@ -417,20 +419,60 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
         __syncwarp();
     } else {
         // ------------------------------------------------------- builder warps
-        // Fold layout: warp w reads TMEM lanes 32 qd .. 32 qd + 31 (qd = w & 3,
-        // rows: 0..63 -Im K, 64..127 Re K, row index p = lane row mod 64) and
-        // columns 32 hf .. 32 hf + 31 (hf = w >> 2), plus column 64 (y) when
-        // hf = 0.  Only the lower triangle q <= p is needed: quadrants 0 and
-        // 2 (p < 32) skip columns 32..63.
+        // Fold layout: warp w reads TMEM lanes 32 qd .. 32 qd + 31 (qd = w & 3):
+        // lane l < 16 the row of u_p, lane l + 16 the row of v_p, p = 16 qd + l
+        // % 16.  Column block c (columns 32 c .. 32 c + 31: u_q, then v_q, q =
+        // 16 c .. 16 c + 15) is needed for c <= qd (lower triangle); warp half
+        // hf = w >> 2 takes blocks hf and hf + 2, and hf = 1 also the y columns
+        // 128 (Re t) and 129 (Im t).
         const int qd = warp & 3, hf = warp >> 2;
-        const int row = 32 * qd + lane;
-        const bool need_main = (qd & 1) || hf == 0;
-        const bool need_y = hf == 0;
-        // Kahan sums: 16 packed pairs for the 32 main columns, one scalar for y
-        uint64_t sum2[16], comp2[16];
+        const bool is_u = lane < 16;
+        const int p = 16 * qd + (lane & 15);
+        const bool live = 16 * qd < D;   // some p of the quadrant is a feature
+        const bool has0 = live && hf <= qd;
+        const bool has1 = live && hf + 2 <= qd;
+        const bool need_y = live && hf == 1;
+        // Kahan sums: 8 packed pairs per column block, one scalar for y
+        uint64_t sum2[2][8], comp2[2][8];
         float sum_y = 0.f, comp_y = 0.f;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) { sum2[j] = 0ull; comp2[j] = 0ull; }
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) { sum2[i][j] = 0ull; comp2[i][j] = 0ull; }
+
+        // the u lane's Re K (own u column + partner's v column) or the v lane's
+        // Im K (partner's v column - own u column)
+        auto pair = [&](float own_u, float own_v) {
+            const float other = __shfl_xor_sync(0xffffffffu, own_v, 16);
+            return is_u ? own_u + other : other - own_u;
+        };
+        auto kahan_block = [&](const float* v, uint64_t* s2, uint64_t* c2) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float a = pair(v[2 * j], v[16 + 2 * j]);
+                const float b = pair(v[2 * j + 1], v[16 + 2 * j + 1]);
+                const uint64_t y = f2sub(f2pack(a, b), c2[j]);
+                const uint64_t t = f2add(s2[j], y);
+                c2[j] = f2sub(f2sub(t, s2[j]), y);
+                s2[j] = t;
+            }
+        };
+        // record copy in shared memory: the u lanes write Re, the v lanes Im
+        auto put_block = [&](int c, const uint64_t* s2, const uint64_t* c2, const float* w) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float s0, s1, c0, c1;
+                f2unpack(s2[j], s0, s1);
+                f2unpack(c2[j], c0, c1);
+                const float v2[2] = {(s0 - c0) + pair(w[2 * j], w[16 + 2 * j]),
+                                     (s1 - c1) + pair(w[2 * j + 1], w[16 + 2 * j + 1])};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int q = 16 * c + 2 * j + h;
+                    if (p < D && q <= p) recs[2 * (p * (p + 1) / 2 + q) + (is_u ? 0 : 1)] = (q == p && !is_u) ? 0.f : v2[h];
+                }
+            }
+        };
 
         auto fold = [&](const TcFold& f) {
             const int bs = f.gc % NBIG;
@@ -438,129 +480,144 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             __syncwarp();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
-            float v[33];
-            if (need_main) {
-                tc_ld16(lane_base + bs * 128 + 32 * hf, v);
-                tc_ld16(lane_base + bs * 128 + 32 * hf + 16, v + 16);
+            const uint32_t acc = lane_base + (uint32_t)(bs * TcGram::ACC_STRIDE);
+            // one column block at a time (registers)
+            float v[32];
+            auto ld_block = [&](uint32_t a) {
+                tc_ld16(a, v);
+                tc_ld16(a + 16, v + 16);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            };
+            if (has0) {
+                ld_block(acc + 32 * hf);
+                kahan_block(v, sum2[0], comp2[0]);
             }
-            if (need_y) tc_ld1(lane_base + bs * 128 + 64, v + 32);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) tc_arrive(tc_smem_u32(&accempty[bs]));
-            if (need_main) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const uint64_t y = f2sub(f2pack(v[2 * j], v[2 * j + 1]), comp2[j]);
-                    const uint64_t t = f2add(sum2[j], y);
-                    comp2[j] = f2sub(f2sub(t, sum2[j]), y);
-                    sum2[j] = t;
-                }
+            if (has1) {
+                ld_block(acc + 32 * (hf + 2));
+                kahan_block(v, sum2[1], comp2[1]);
             }
             if (need_y) {
-                const float y = v[32] - comp_y;
+                tc_ld2(acc + 128, v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const float y = pair(v[0], v[1]) - comp_y;
                 const float t = sum_y + y;
                 comp_y = (t - sum_y) - y;
                 sum_y = t;
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tc_arrive(tc_smem_u32(&accempty[bs]));
             if (!f.last) return;
-            // end of the slice: add the cross terms, release their accumulator
-            float w[33];
+            // end of the slice: add the cross terms (when the slice had more
+            // than one chunk), write the record copy, release the accumulator
+            const uint32_t sm = lane_base + (uint32_t)TcGram::SMALL_COL;
+            auto cross_block = [&](uint32_t a) {
+                if (f.multi) {
+                    ld_block(a);
+                } else {
 #pragma unroll
-            for (int j = 0; j < 33; ++j) w[j] = 0.f;
-            if (f.multi) {
-                if (need_main) {
-                    tc_ld16(lane_base + TcGram::SMALL_COL + 32 * hf, w);
-                    tc_ld16(lane_base + TcGram::SMALL_COL + 32 * hf + 16, w + 16);
+                    for (int j = 0; j < 32; ++j) v[j] = 0.f;
                 }
-                if (need_y) tc_ld1(lane_base + TcGram::SMALL_COL + 64, w + 32);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            };
+            if (has0) {
+                cross_block(sm + 32 * hf);
+                put_block(hf, sum2[0], comp2[0], v);
+            }
+            if (has1) {
+                cross_block(sm + 32 * (hf + 2));
+                put_block(hf + 2, sum2[1], comp2[1], v);
+            }
+            if (need_y) {
+                v[0] = 0.f;
+                v[1] = 0.f;
+                if (f.multi) {
+                    tc_ld2(sm + 128, v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                }
+                const float yv = (sum_y - comp_y) + pair(v[0], v[1]);
+                if (p < D) recs[2 * (NPK + p) + (is_u ? 0 : 1)] = yv;
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) tc_arrive(tc_smem_u32(&sempty[0]));
-            if (need_main) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    float s0, s1, c0, c1;
-                    f2unpack(sum2[j], s0, s1);
-                    f2unpack(comp2[j], c0, c1);
-                    scr[row * TcGram::SCR_LD + 32 * hf + 2 * j] = (s0 - c0) + w[2 * j];
-                    scr[row * TcGram::SCR_LD + 32 * hf + 2 * j + 1] = (s1 - c1) + w[2 * j + 1];
-                }
-            }
-            if (need_y) scr[row * TcGram::SCR_LD + 64] = (sum_y - comp_y) + w[32];
+            for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int j = 0; j < 16; ++j) { sum2[j] = 0ull; comp2[j] = 0ull; }
+                for (int j = 0; j < 8; ++j) { sum2[i][j] = 0ull; comp2[i][j] = 0ull; }
             sum_y = 0.f;
             comp_y = 0.f;
             asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
-            // record: row p of the packed lower triangle is contiguous
-            float2* out = rec + (size_t)f.k * (NPK + D);
-            for (int p = warp; p < D; p += TcGram::NBUILD) {
-                float2* orow = out + p * (p + 1) / 2;
-                for (int q = lane; q <= p; q += 32)
-                    orow[q] = make_float2(scr[(64 + p) * TcGram::SCR_LD + q], -scr[p * TcGram::SCR_LD + q]);
-                if (lane == 0)
-                    out[NPK + p] = make_float2(scr[(64 + p) * TcGram::SCR_LD + 64], -scr[p * TcGram::SCR_LD + 64]);
-            }
+            // the record (NPK + D complex values, an even count for D = R^2,
+            // so records start on 16-byte boundaries) in 16-byte pieces
+            const float4* src = (const float4*)recs;
+            float4* out = (float4*)(rec + (size_t)f.k * (NPK + D));
+            for (int x = tid; x < (NPK + D) / 2; x += NB) out[x] = src[x];
             asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
         };
 
-        // operand rows of this thread: entry e = lane, rows q = r8 + 8 j
-        // (j = 0..7) with r8 = w, so the swizzled offset inside a row group
-        // is fixed per thread
+        // operand rows of this thread: entries lane and 32 + lane (K blocks 0
+        // and 1), features q = r8 + 8 j (j = 0..7) with r8 = w; the row of
+        // u_q is 32 (q / 16) + q % 16 = 8 (4 (j / 2) + j % 2) + r8 and the row
+        // of v_q 16 further, so the swizzled offset inside a row group is
+        // fixed per thread.  Warps 0 and 1 also write Re t (row 128) and Im t
+        // (row 129).
         const int r8 = warp;
         const uint32_t t_off = (uint32_t)(r8 * 128 + ((((lane >> 2) ^ r8)) << 4) + (lane & 3) * 4);
-        const int e = lane;
 
         // the h_p, w_c (and t) this thread needs for chunk c, from the input
         // ring stage of the chunk (rank 8: p = j and c = r8, so one w and the
         // whole h); the stage is released to the loader once read
         constexpr int NW = R == 8 ? 1 : 8;
-        struct Vals { float2 h[8], w[NW], t; };
+        struct Vals { float2 h[2][8], w[2][NW], t[2]; };
         auto load = [&](const TcChunk& c, int gc, Vals& vl) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) vl.h[j] = make_float2(0.f, 0.f);
+            for (int eb = 0; eb < 2; ++eb) {
 #pragma unroll
-            for (int j = 0; j < NW; ++j) vl.w[j] = make_float2(0.f, 0.f);
-            vl.t = make_float2(0.f, 0.f);
+                for (int j = 0; j < 8; ++j) vl.h[eb][j] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < NW; ++j) vl.w[eb][j] = make_float2(0.f, 0.f);
+                vl.t[eb] = make_float2(0.f, 0.f);
+            }
             const int st = gc % TcGram::NIN;
             tc_wait(tc_smem_u32(&infull[st]), (uint32_t)((gc / TcGram::NIN) & 1), abort_s, err);
             const unsigned char* sb = inring + (size_t)st * TcGram::INSTG;
             const float2* hs = (const float2*)(sb + in_off(H, c.base, R * 8));
             const float2* ws = (const float2*)(sb + TcGram::HB + in_off(Wm, c.base, R * 8));
             const float2* ts = (const float2*)(sb + 2 * TcGram::HB + in_off(tv, c.base, 8));
-            if (e < c.cnt()) {
-                if (R == 8) {
-                    const float4* hp = (const float4*)(hs + e * R);
+            const int cnt = c.cnt();
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float4 h2 = hp[j];
-                        vl.h[2 * j] = make_float2(h2.x, h2.y);
-                        vl.h[2 * j + 1] = make_float2(h2.z, h2.w);
-                    }
-                    vl.w[0] = ws[e * R + r8];
-                } else {
+            for (int eb = 0; eb < 2; ++eb) {
+                const int e = 32 * eb + lane;
+                if (e < cnt) {
+                    if (R == 8) {
+                        const float4* hp = (const float4*)(hs + e * R);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int q = r8 + 8 * j;
-                        if (q < D) {
-                            vl.h[j] = hs[e * R + q / R];
-                            vl.w[j % NW] = ws[e * R + q % R];
+                        for (int j = 0; j < 4; ++j) {
+                            const float4 h2 = hp[j];
+                            vl.h[eb][2 * j] = make_float2(h2.x, h2.y);
+                            vl.h[eb][2 * j + 1] = make_float2(h2.z, h2.w);
+                        }
+                        vl.w[eb][0] = ws[e * R + r8];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int q = r8 + 8 * j;
+                            if (q < D) {
+                                vl.h[eb][j] = hs[e * R + q / R];
+                                vl.w[eb][j % NW] = ws[e * R + q % R];
+                            }
                         }
                     }
+                    if (warp < 2) vl.t[eb] = ts[e];
                 }
-                if (warp == 0) vl.t = ts[e];
             }
             __syncwarp();
             if (lane == 0) tc_arrive(tc_smem_u32(&inempty[st]));
         };
 
         TcChunk cur = first_of(blockIdx.x, 0);
-        TcFold f1, f2;   // chunks g-1 and g-2, folded two chunks late
+        TcFold f1;   // chunk g-1, folded one chunk late
         f1.valid = false;
-        f2.valid = false;
         Vals vc;
         int g = 0;
         while (cur.valid) {
@@ -569,39 +626,37 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             const int b = g & 1;
             if (g >= 2) tc_wait(tc_smem_u32(&empty[b]), (uint32_t)(((g - 2) >> 1) & 1), abort_s, err);
             unsigned char* st = ops + b * TcGram::STAGE;
-            auto put = [&](uint32_t off, int part, uint32_t hi, uint32_t lo) {
-                *(uint32_t*)(st + (2 * part) * TcGram::KB + off) = hi;
-                *(uint32_t*)(st + (2 * part + 1) * TcGram::KB + off) = lo;
-            };
-            if (warp == 0) {  // T row 128 (row group 16, r8 = 0)
-                uint32_t h0, l0, h1, l1;
-                tc_split(vc.t.x, h0, l0);
-                tc_split(vc.t.y, h1, l1);
-                put(16 * 1024 + t_off, 0, h0, l0);
-                put(16 * 1024 + t_off, 1, h1, l1);
-            }
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int q = r8 + 8 * j;
-                if (q < D) {
-                    const float2 hv = vc.h[j], wq = vc.w[j % NW];
-                    const float u = hv.x * wq.x - hv.y * wq.y;
-                    const float v = hv.x * wq.y + hv.y * wq.x;
-                    uint32_t uh, ul, vh, vl;
-                    tc_split(u, uh, ul);
-                    tc_split(v, vh, vl);
-                    const uint32_t offq = (uint32_t)(j * 1024) + t_off;
-                    put(offq + 8192, 0, uh, ul);                      // P_q = (u, v)
-                    put(offq + 8192, 1, vh, vl);
-                    put(offq, 0, vh, vl);                             // Q_q = (v, -u)
-                    put(offq, 1, uh ^ 0x80000000u, ul ^ 0x80000000u);
+            for (int eb = 0; eb < 2; ++eb) {
+                auto put = [&](uint32_t off, uint32_t hi, uint32_t lo) {
+                    *(uint32_t*)(st + (2 * eb) * TcGram::KB + off) = hi;
+                    *(uint32_t*)(st + (2 * eb + 1) * TcGram::KB + off) = lo;
+                };
+                if (warp < 2) {  // Re t at row 128, Im t at row 129 (row group 16, r8 = warp)
+                    uint32_t th, tl;
+                    tc_split(warp == 0 ? vc.t[eb].x : vc.t[eb].y, th, tl);
+                    put(16 * 1024 + t_off, th, tl);
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int q = r8 + 8 * j;
+                    if (q < D) {
+                        const float2 hv = vc.h[eb][j], wq = vc.w[eb][j % NW];
+                        const float u = hv.x * wq.x - hv.y * wq.y;
+                        const float v = hv.x * wq.y + hv.y * wq.x;
+                        uint32_t uh, ul, vh, vl;
+                        tc_split(u, uh, ul);
+                        tc_split(v, vh, vl);
+                        const uint32_t offu = (uint32_t)((4 * (j >> 1) + (j & 1)) * 1024) + t_off;
+                        put(offu, uh, ul);          // u_q
+                        put(offu + 2048, vh, vl);   // v_q, 16 rows further
+                    }
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) tc_arrive(tc_smem_u32(&full[b]));
-            if (f2.valid) fold(f2);
-            f2 = f1;
+            if (f1.valid) fold(f1);
             f1.valid = true;
             f1.k = cur.k;
             f1.gc = g;
@@ -610,7 +665,6 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             cur = nxt;
             ++g;
         }
-        if (f2.valid) fold(f2);
         if (f1.valid) fold(f1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
