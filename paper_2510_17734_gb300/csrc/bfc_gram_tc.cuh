@@ -563,6 +563,7 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
         // (row 129).
         const int r8 = warp;
         const uint32_t t_off = (uint32_t)(r8 * 128 + ((((lane >> 2) ^ r8)) << 4) + (lane & 3) * 4);
+        const int rot = (lane >> 1) & 3;
 
         // the h_p, w_c (and t) this thread needs for chunk c, from the input
         // ring stage of the chunk (rank 8: p = j and c = r8, so one w and the
@@ -590,10 +591,14 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
                 const int e = 32 * eb + lane;
                 if (e < cnt) {
                     if (R == 8) {
+                        // the 16-byte pieces of a 64-byte row in the order
+                        // rot, rot + 1, ... (mod 4): the 32 lanes then fall on
+                        // 8 distinct bank groups (4 wavefronts per load instead
+                        // of 16); slot j holds feature piece (j + rot) mod 4
                         const float4* hp = (const float4*)(hs + e * R);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const float4 h2 = hp[j];
+                            const float4 h2 = hp[(j + rot) & 3];
                             vl.h[eb][2 * j] = make_float2(h2.x, h2.y);
                             vl.h[eb][2 * j + 1] = make_float2(h2.z, h2.w);
                         }
@@ -639,7 +644,9 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
                 }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int q = r8 + 8 * j;
+                    // feature q = r8 + 8 jf of slot j (rank 8: the rotated pieces)
+                    const int jf = R == 8 ? 2 * (((j >> 1) + rot) & 3) + (j & 1) : j;
+                    const int q = r8 + 8 * jf;
                     if (q < D) {
                         const float2 hv = vc.h[eb][j], wq = vc.w[eb][j % NW];
                         const float u = hv.x * wq.x - hv.y * wq.y;
@@ -647,7 +654,7 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
                         uint32_t uh, ul, vh, vl;
                         tc_split(u, uh, ul);
                         tc_split(v, vh, vl);
-                        const uint32_t offu = (uint32_t)((4 * (j >> 1) + (j & 1)) * 1024) + t_off;
+                        const uint32_t offu = (uint32_t)((4 * (jf >> 1) + (jf & 1)) * 1024) + t_off;
                         put(offu, uh, ul);          // u_q
                         put(offu + 2048, vh, vl);   // v_q, 16 rows further
                     }
