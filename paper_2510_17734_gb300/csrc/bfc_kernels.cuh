@@ -711,6 +711,25 @@ k_mid_gram(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
 }
 
 // ------------------------------------------------------------------------
+// Packed pairs of FP32 values for the complex64 trailing update of
+// warp_chol: one fma.rn.f32x2 does two lanes' worth of fused multiply-adds.
+__device__ __forceinline__ uint64_t c2pack(float a, float b)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void c2unpack(uint64_t r, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t c2fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // Row of slot s owned by a lane in the warp-level factorization: even slots
 // take rows 32 s + lane, odd slots mirror them (32 s + 31 - lane), so the two
 // rows of a lane have complementary lengths and the work per lane is balanced.
@@ -793,6 +812,71 @@ __device__ bool warp_chol(E* Lm, int D, S tol, int lane)
         }
         __syncwarp();
         // (3) rank-NBK trailing update
+        if constexpr (sizeof(S) == 4) {
+            // complex64: L[r][q] -= sum_k x_k conj(l_k) (l = L[q][j0 + k]) as
+            // two packed fused multiply-adds per term, with the factors of
+            // x_k prepared once per row: l (.) (-x.re, x.re) goes into
+            // (re, im) and l (.) (-x.im, -x.im) into a second accumulator
+            // that holds (im, re)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int r = owned_row(s, lane);
+                if (r >= j1 && r < D) {
+                    uint64_t p1[NBK], p2[NBK];
+#pragma unroll
+                    for (int k = 0; k < NBK; ++k) {
+                        const float xr = k < nb ? x[s][k].x : 0.f, xi = k < nb ? x[s][k].y : 0.f;
+                        p1[k] = c2pack(-xr, xr);
+                        p2[k] = c2pack(-xi, -xi);
+                    }
+                    E* rowp = Lm + tri(r, 0);
+                    auto finish = [&](uint64_t acc, uint64_t sw) {
+                        float ar, ai, si, sr;
+                        c2unpack(acc, ar, ai);
+                        c2unpack(sw, si, sr);
+                        E v;
+                        v.x = ar + sr;
+                        v.y = ai + si;
+                        return v;
+                    };
+                    int q = j1;
+                    for (; q + 1 <= r; q += 2) {
+                        const uint64_t* qa = reinterpret_cast<const uint64_t*>(Lm + tri(q, 0) + j0);
+                        const uint64_t* qb = reinterpret_cast<const uint64_t*>(Lm + tri(q + 1, 0) + j0);
+                        const E ea = rowp[q], eb = rowp[q + 1];
+                        uint64_t ca = c2pack(ea.x, ea.y), cb = c2pack(eb.x, eb.y), sa = 0ull, sb = 0ull;
+                        uint64_t va[NBK], vb[NBK];
+#pragma unroll
+                        for (int k = 0; k < NBK; ++k)
+                            if (k < nb) { va[k] = qa[k]; vb[k] = qb[k]; }
+#pragma unroll
+                        for (int k = 0; k < NBK; ++k)
+                            if (k < nb) {
+                                ca = c2fma(va[k], p1[k], ca);
+                                sa = c2fma(va[k], p2[k], sa);
+                                cb = c2fma(vb[k], p1[k], cb);
+                                sb = c2fma(vb[k], p2[k], sb);
+                            }
+                        rowp[q] = finish(ca, sa);
+                        rowp[q + 1] = finish(cb, sb);
+                    }
+                    if (q <= r) {
+                        const uint64_t* qr = reinterpret_cast<const uint64_t*>(Lm + tri(q, 0) + j0);
+                        const E e0 = rowp[q];
+                        uint64_t c0 = c2pack(e0.x, e0.y), s0 = 0ull;
+#pragma unroll
+                        for (int k = 0; k < NBK; ++k)
+                            if (k < nb) {
+                                const uint64_t v = qr[k];
+                                c0 = c2fma(v, p1[k], c0);
+                                s0 = c2fma(v, p2[k], s0);
+                            }
+                        rowp[q] = finish(c0, s0);
+                    }
+                }
+            }
+            continue;
+        }
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const int r = owned_row(s, lane);
