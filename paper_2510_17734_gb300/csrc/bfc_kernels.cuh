@@ -188,6 +188,44 @@ __global__ void k_env_init(typename cvec<T>::type* __restrict__ WL,
 // lanes busy: small systems are solved one per thread, large ones with rows
 // spread over the lanes.
 
+// Packed pairs of FP32 values (the f32x2 arithmetic of sm_100 and later): one
+// instruction does two lanes' worth of adds or fused multiply-adds.
+__device__ __forceinline__ uint64_t c2pack(float a, float b)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void c2unpack(uint64_t r, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t c2fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint64_t c2add(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t c2sub(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t c2mul(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 template <typename E> __device__ __forceinline__ void csub_mul_conj(E& acc, E a, E b)
 {
     // acc -= a * conj(b)
@@ -208,22 +246,52 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     const float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
-// acc -= k * (sh + sl) for complex k (float) and a double-float complex s;
-// acc = {re_hi, re_lo, im_hi, im_lo}.  p = fl(k sh) and e = k sh - p exactly
-// (TwoProd by FMA); the lo-part products only need ordinary accuracy.
-__device__ __forceinline__ void df_sub_cmul(float4& acc, float2 k, float2 sh, float2 sl)
+// Double-float complex update acc -= k (sh + sl) for a complex64 k and a
+// double-float complex s, on packed (re, im) pairs: hi = (re_hi, im_hi), lo =
+// (re_lo, im_lo), so each step is one f32x2 instruction for both components.  Every operation is an explicitly rounded packed
+// instruction (inline PTX is never contracted), so TwoSum and the FMA-based
+// TwoProd stay exact.  DfS2 holds the packed forms of s = sh + sl that the
+// products need (prepared once per column and shared by a lane's rows).
+struct DfS2 {
+    uint64_t sh, shn, shr, shrn, sl, slr;
+};
+__device__ __forceinline__ DfS2 df2_prep(float2 sh, float2 sl)
 {
-    float t, e;
-    const float p1 = __fmul_rn(k.x, sh.x), e1 = fmaf(k.x, sh.x, -p1);
-    const float p2 = __fmul_rn(k.y, sh.y), e2 = fmaf(k.y, sh.y, -p2);
-    two_sum(acc.x, -p1, t, e); acc.x = t; acc.y += e;
-    two_sum(acc.x, p2, t, e); acc.x = t; acc.y += e;
-    acc.y -= e1 - e2 + (k.x * sl.x - k.y * sl.y);
-    const float p3 = __fmul_rn(k.x, sh.y), e3 = fmaf(k.x, sh.y, -p3);
-    const float p4 = __fmul_rn(k.y, sh.x), e4 = fmaf(k.y, sh.x, -p4);
-    two_sum(acc.z, -p3, t, e); acc.z = t; acc.w += e;
-    two_sum(acc.z, -p4, t, e); acc.z = t; acc.w += e;
-    acc.w -= e3 + e4 + (k.x * sl.y + k.y * sl.x);
+    DfS2 r;
+    r.sh = c2pack(sh.x, sh.y);
+    r.shn = c2pack(-sh.x, -sh.y);
+    r.shr = c2pack(-sh.y, sh.x);
+    r.shrn = c2pack(sh.y, -sh.x);
+    r.sl = c2pack(sl.x, sl.y);
+    r.slr = c2pack(-sl.y, sl.x);
+    return r;
+}
+__device__ __forceinline__ void two_sum2(uint64_t a, uint64_t b, uint64_t& s, uint64_t& e)
+{
+    s = c2add(a, b);
+    const uint64_t bb = c2sub(s, a);
+    e = c2add(c2sub(a, c2sub(s, bb)), c2sub(b, bb));
+}
+// hi + lo -= k (sh + sl).  With A = k.re (sh.re, sh.im) and B = k.im (-sh.im,
+// sh.re), k sh = A + B; fl(-A), fl(-B) enter hi by TwoSum and their exact
+// product errors, with k sl, enter lo.
+__device__ __forceinline__ void df2_sub_cmul(uint64_t& hi, uint64_t& lo, float2 k, const DfS2& s)
+{
+    const uint64_t kx = c2pack(k.x, k.x), ky = c2pack(k.y, k.y);
+    const uint64_t pa = c2mul(kx, s.shn);     // -fl(A)
+    const uint64_t ea = c2fma(kx, s.sh, pa);  // A - fl(A)
+    const uint64_t pb = c2mul(ky, s.shrn);    // -fl(B)
+    const uint64_t eb = c2fma(ky, s.shr, pb); // B - fl(B)
+    uint64_t t, e;
+    two_sum2(hi, pa, t, e);
+    hi = t;
+    lo = c2add(lo, e);
+    two_sum2(hi, pb, t, e);
+    hi = t;
+    lo = c2add(lo, e);
+    uint64_t w = c2fma(kx, s.sl, ea);
+    w = c2fma(ky, s.slr, w);
+    lo = c2sub(lo, c2add(w, eb));
 }
 
 // Hermitian Cholesky + two triangular solves for one small system held by one
@@ -711,25 +779,6 @@ k_mid_gram(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>:
 }
 
 // ------------------------------------------------------------------------
-// Packed pairs of FP32 values for the complex64 trailing update of
-// warp_chol: one fma.rn.f32x2 does two lanes' worth of fused multiply-adds.
-__device__ __forceinline__ uint64_t c2pack(float a, float b)
-{
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void c2unpack(uint64_t r, float& a, float& b)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ uint64_t c2fma(uint64_t a, uint64_t b, uint64_t c)
-{
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
 // Row of slot s owned by a lane in the warp-level factorization: even slots
 // take rows 32 s + lane, odd slots mirror them (32 s + 31 - lane), so the two
 // rows of a lane have complementary lengths and the work per lane is balanced.
@@ -1241,15 +1290,17 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
                     // one pass over q for all rows of the lane: s_q is read once
                     // for them, and K_pq comes from the stored lower triangle
                     // (conjugated above the diagonal), so no lane idles
-                    float4 acc[NS];
+                    // packed double-float accumulators: (re, im) of hi and of lo
+                    uint64_t ahi[NS], alo[NS];
 #pragma unroll
                     for (int s = 0; s < NS; ++s) {
                         const int p = lane + 32 * s;
-                        acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        ahi[s] = 0ull;
+                        alo[s] = 0ull;
                         if (p < D) {
                             const V yp = K[NPK + p];
-                            acc[s] = make_float4(yp.x, 0.f, yp.y, 0.f);
-                            df_sub_cmul(acc[s], make_float2(lamf, 0.f), sh[s], sl[s]);
+                            ahi[s] = c2pack(yp.x, yp.y);
+                            df2_sub_cmul(ahi[s], alo[s], make_float2(lamf, 0.f), df2_prep(sh[s], sl[s]));
                         }
                     }
                     // K_pq for 8 columns are fetched (from L2) before their products
@@ -1275,10 +1326,10 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
                             const int q = q0 + i;
                             if (q < D) {
                                 const float4 sq = s_df[q];
+                                const DfS2 sp = df2_prep(make_float2(sq.x, sq.y), make_float2(sq.z, sq.w));
 #pragma unroll
                                 for (int s = 0; s < NS; ++s)
-                                    if (lane + 32 * s < D)
-                                        df_sub_cmul(acc[s], kv[s][i], make_float2(sq.x, sq.y), make_float2(sq.z, sq.w));
+                                    if (lane + 32 * s < D) df2_sub_cmul(ahi[s], alo[s], kv[s][i], sp);
                             }
                         }
                     }
@@ -1286,8 +1337,7 @@ k_mid_solve(const typename cvec<T>::type* __restrict__ rec, const typename cvec<
                     float rmax = 0.f;
 #pragma unroll
                     for (int s = 0; s < NS; ++s) {
-                        rr[s][0] = acc[s].x + acc[s].y;
-                        rr[s][1] = acc[s].z + acc[s].w;
+                        c2unpack(c2add(ahi[s], alo[s]), rr[s][0], rr[s][1]);
                         rmax = fmaxf(rmax, fmaxf(fabsf(rr[s][0]), fabsf(rr[s][1])));
                     }
 #pragma unroll
