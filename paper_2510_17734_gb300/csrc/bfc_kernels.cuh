@@ -835,6 +835,48 @@ __device__ bool warp_chol(E* Lm, int D, S tol, int lane)
         const int nb = j1 - j0;
         // (2) panel rows, solved in registers by their owner lanes
         E x[NS][NBK];
+        if constexpr (sizeof(S) == 4) {
+            // complex64: the same substitution with the terms as packed fused
+            // multiply-adds (the trailing update's form below)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int r = owned_row(s, lane);
+                if (r >= j1 && r < D) {
+                    E* rowp = Lm + tri(r, 0);
+                    uint64_t p1[NBK], p2[NBK];
+#pragma unroll
+                    for (int cc = 0; cc < NBK; ++cc) {
+                        x[s][cc] = E{};
+                        p1[cc] = 0ull;
+                        p2[cc] = 0ull;
+                        if (cc < nb) {
+                            const uint64_t* drow = reinterpret_cast<const uint64_t*>(Lm + tri(j0 + cc, 0) + j0);
+                            const E e0 = rowp[j0 + cc];
+                            uint64_t acc = c2pack(e0.x, e0.y), sw = 0ull;
+#pragma unroll
+                            for (int k = 0; k < cc; ++k) {
+                                const uint64_t b = drow[k];
+                                acc = c2fma(b, p1[k], acc);
+                                sw = c2fma(b, p2[k], sw);
+                            }
+                            float ar, ai, si, sr;
+                            c2unpack(acc, ar, ai);
+                            c2unpack(sw, si, sr);
+                            const S inv = Lm[tri(j0 + cc, j0 + cc)].y;
+                            E v;
+                            v.x = (ar + sr) * inv;
+                            v.y = (ai + si) * inv;
+                            x[s][cc] = v;
+                            p1[cc] = c2pack(-v.x, v.x);
+                            p2[cc] = c2pack(-v.y, -v.y);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < NBK; ++k)
+                        if (k < nb) rowp[j0 + k] = x[s][k];
+                }
+            }
+        } else {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const int r = owned_row(s, lane);
@@ -858,6 +900,7 @@ __device__ bool warp_chol(E* Lm, int D, S tol, int lane)
                 for (int k = 0; k < NBK; ++k)
                     if (k < nb) roww[j0 + k] = x[s][k];
             }
+        }
         }
         __syncwarp();
         // (3) rank-NBK trailing update
