@@ -277,6 +277,10 @@ static bfc_status build(Ctx* c, const Inputs& in)
             const double ratio = c->gram_tc ? c->grp_max_ratio : c->grp_cuda_ratio;
             if ((c->r == 4 || c->r == 8) && c->P.gram_impl == 0 && (double)G < ratio * (double)N) {
                 gst.push_back((int32_t)N);
+                // the largest entry range of a k_group_sums block (its shared-memory staging)
+                const int64_t gpb = 128 / c->r;
+                for (int64_t g0 = 0; g0 < G; g0 += gpb)
+                    gl.max_block = std::max(gl.max_block, (int64_t)gst[std::min(g0 + gpb, G)] - gst[g0]);
                 int64_t g = 0;
                 for (int64_t k = 0; k <= S; ++k) {
                     while (g < G && (int64_t)(hkeys[gst[g]] / (uint64_t)loc) < k) ++g;

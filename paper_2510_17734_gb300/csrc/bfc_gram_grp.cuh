@@ -85,31 +85,32 @@ template <typename T, int R> struct GsumCfg {
 //   M[a][a'] = sum_e conj(u_e[a]) u_e[a'],   v[a] = sum_e conj(u_e[a]) t_e
 // of the other environment u (w, resp. h).  Record per group, compute type:
 // [s (R) | M (R x R, row-major) | v (R)].  A block's groups are contiguous
-// in the level order, and so are their entries: when they fit (CAP), the
-// rows u_e and values t_e of all of them are copied to shared memory at once
-// (cp.async), so their loads overlap; otherwise they are read from global
-// memory.  In the precision form the sums run in complex64 over blocks of 16
+// in the level order, and so are their entries: when they fit (cap <= CAP
+// entries, the dynamic shared memory of the launch, sized for the level's
+// largest block), the rows u_e and values t_e of all of them are copied to
+// shared memory at once (cp.async), so their loads overlap; otherwise they
+// are read from global memory.  In the precision form the sums run in complex64 over blocks of 16
 // entries, Kahan-compensated across blocks.
 template <typename T, int R>
 __global__ void __launch_bounds__(GsumCfg<T, R>::NTH)
 k_group_sums(const typename cvec<T>::type* __restrict__ H, const typename cvec<T>::type* __restrict__ Wm,
              const typename cvec<T>::type* __restrict__ tv, const int32_t* __restrict__ gstart, int G, int by_col,
-             typename cvec<T>::type* __restrict__ out)
+             typename cvec<T>::type* __restrict__ out, int cap)
 {
     typedef typename cvec<T>::type V;
     typedef GsumCfg<T, R> C;
     typedef GrpRec<V, R> RL;
     constexpr int RS = RL::RS;
     extern __shared__ __align__(16) unsigned char smem[];
-    V* su = (V*)smem;                          // [CAP][R] rows
-    V* st = su + (size_t)C::CAP * R;           // [CAP] values
+    V* su = (V*)smem;                          // [cap][R] rows
+    V* st = su + (size_t)cap * R;              // [cap] values
     const V* Sv = by_col ? Wm : H;
     const V* Uv = by_col ? H : Wm;
 
     const int gb0 = blockIdx.x * C::GB;
     const int gb1 = min(gb0 + C::GB, G);
     const int E0 = gstart[gb0], E1 = gstart[gb1];
-    const bool staged = E1 - E0 <= C::CAP;
+    const bool staged = E1 - E0 <= cap;
     if (staged) {
         // rows: (E1 - E0) R values, 16-byte pieces (a row is R * VS >= 32 bytes)
         const int rpieces = (int)((size_t)(E1 - E0) * R * C::VS / 16);

@@ -36,6 +36,7 @@ struct GroupLevel {
     int64_t ngroups = 0;
     int32_t* gstart = nullptr;
     int32_t* gseg = nullptr;
+    int64_t max_block = 0;   // most entries of a k_group_sums block (128 / r consecutive groups)
 };
 
 // Device buffers of one completion problem.  Level l = 0 is the S^1 (row)

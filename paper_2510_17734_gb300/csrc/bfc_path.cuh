@@ -150,9 +150,13 @@ template <typename T, int R> struct Path {
                         const GroupLevel& gl = c->grp[m];
                         constexpr int RG = GRP ? R : 4;
                         typedef GsumCfg<T, RG> GS;
-                        k_group_sums<T, RG><<<nblocks(gl.ngroups, GS::GB), GS::NTH, GS::SMEM, c->stream>>>(
+                        static_assert(GS::NTH == 128, "host block partition of the group sums");
+                        // shared memory for the level's largest block (at most CAP entries)
+                        const int cap = (int)std::min<int64_t>(gl.max_block, GS::CAP);
+                        k_group_sums<T, RG><<<nblocks(gl.ngroups, GS::GB), GS::NTH,
+                                              (size_t)cap * (RG + 1) * GS::VS, c->stream>>>(
                             hin, W + (size_t)m * NR, (const V*)c->tval[m], gl.gstart, (int)gl.ngroups, gl.by_col,
-                            (V*)c->grec);
+                            (V*)c->grec, cap);
                         if (gl.by_col)
                             k_mid_gram_grp<T, RG, 1><<<(unsigned)S, GrpCfg<T, RG>::NTH, GrpCfg<T, RG>::SMEM,
                                                        c->stream>>>((const V*)c->grec, gl.gseg, (V*)c->rec, (int)S);
