@@ -69,8 +69,9 @@ struct TcGram {
     static constexpr int ACC_STRIDE = 160;
     static constexpr int SMALL_COL = 320;         // per-slice cross-term accumulator
     static constexpr int TMEM_COLS = 512;
-    static constexpr int NBUILD = 8;              // builder / fold warps: 2 per TMEM lane quadrant
-    static constexpr int NTH = 32 * (NBUILD + 2); // + the MMA warp + the input-loader warp
+    static constexpr int NBUILD = 8;              // operand builder warps
+    static constexpr int NFOLD = 8;               // fold warps: 2 per TMEM lane quadrant
+    static constexpr int NTH = 32 * (NBUILD + NFOLD + 2);   // + the MMA warp + the input-loader warp
     static constexpr int RECB = (64 * 65 / 2 + 64) * 8;  // packed record copy (rank 8; a multiple of 16 bytes)
     static constexpr int SEGC = 1024;             // cached (start, end) of this CTA's first slices
     static constexpr int NIN = 4;
@@ -150,17 +151,15 @@ __device__ __forceinline__ void tc_arrive(uint32_t bar)
 }
 
 // Consecutive accumulator columns of this thread's TMEM lane.
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v)
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float* v)
 {
-    uint32_t r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                   "=r"(r[14]), "=r"(r[15])
+                   "=r"(r[7])
                  : "r"(taddr));
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 __device__ __forceinline__ void tc_ld2(uint32_t taddr, float* v)
 {
@@ -219,7 +218,7 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
 {
     static_assert(R >= 1 && R <= 8, "tensor-core Gram needs R*R <= 64");
     constexpr int D = R * R, NPK = D * (D + 1) / 2, CE = TcGram::CE, NBIG = TcGram::NBIG;
-    constexpr int NB = 32 * TcGram::NBUILD;   // builder threads
+    constexpr int NF = 32 * TcGram::NFOLD;    // fold threads
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw_s = tc_smem_u32(smem_raw);
     unsigned char* ops = smem_raw + ((1024u - (raw_s & 1023u)) & 1023u);  // 2 operand stages
@@ -229,8 +228,8 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
     uint64_t* full = bars;            // [2]     builders -> MMA warp (count NBUILD)
     uint64_t* empty = bars + 2;       // [2]     MMA commit -> builders (operand stage free)
     uint64_t* accfull = bars + 4;     // [NBIG]  MMA commit -> builders (chunk accumulated)
-    uint64_t* accempty = bars + 6;    // [NBIG]  builders' fold -> MMA warp (count NBUILD)
-    uint64_t* sempty = bars + 8;      // [1]     builders read the cross terms -> MMA warp (count NBUILD)
+    uint64_t* accempty = bars + 6;    // [NBIG]  fold warps -> MMA warp (count NFOLD)
+    uint64_t* sempty = bars + 8;      // [1]     fold warps read the cross terms -> MMA warp (count NFOLD)
     uint64_t* infull = bars + 9;      // [NIN]   bulk copies of a chunk's inputs landed (loader, tx bytes)
     uint64_t* inempty = bars + 9 + TcGram::NIN;   // [NIN] builders read the stage (count NBUILD)
     uint32_t* tmem_slot = (uint32_t*)(bars + TcGram::NBARS);
@@ -253,11 +252,12 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
     }
     if (tid == 0) {
         for (int i = 0; i < TcGram::NBARS; ++i) {
-            // full, accempty, sempty, inempty: one arrival per builder warp;
-            // empty, accfull (MMA commits), infull (loader): one
-            const bool per_builder = i < 2 || (i >= 6 && i < 9) || i >= 9 + TcGram::NIN;
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
-                         ::"r"(tc_smem_u32(&bars[i])), "r"(per_builder ? (uint32_t)TcGram::NBUILD : 1u));
+            // full, inempty: one arrival per builder warp; accempty, sempty: one
+            // per fold warp; empty, accfull (MMA commits), infull (loader): one
+            const uint32_t cnt = (i < 2 || i >= 9 + TcGram::NIN) ? (uint32_t)TcGram::NBUILD
+                                 : (i >= 6 && i < 9)             ? (uint32_t)TcGram::NFOLD
+                                                                 : 1u;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem_u32(&bars[i])), "r"(cnt));
         }
         *abort_s = 0;
     }
@@ -310,7 +310,7 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
     auto in_off = [&](const void* base_ptr, int64_t first, int bytes_per) {
         return (int)(((uintptr_t)base_ptr + (uintptr_t)first * bytes_per) & 15u);
     };
-    if (warp == TcGram::NBUILD + 1) {
+    if (warp == TcGram::NBUILD + TcGram::NFOLD + 1) {
         // ------------------------------------------------------ loader warp
         // Bulk copies of every chunk's h rows, w rows and t values into the
         // input ring, NIN chunks ahead of the builders.
@@ -357,7 +357,7 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             }
         }
         __syncwarp();
-    } else if (warp == TcGram::NBUILD) {
+    } else if (warp == TcGram::NBUILD + TcGram::NFOLD) {
         // ------------------------------------------------------------ MMA warp
         // The first chunk of a slice puts all three products into its hi*hi
         // accumulator; later chunks send the cross terms to the slice's
@@ -417,15 +417,17 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             }
         }
         __syncwarp();
-    } else {
-        // ------------------------------------------------------- builder warps
+    } else if (warp >= TcGram::NBUILD) {
+        // ---------------------------------------------------------- fold warps
+        // Every chunk's hi*hi accumulator is folded as soon as its MMAs are
+        // complete, while the builders fill the next operand stage.
         // Fold layout: warp w reads TMEM lanes 32 qd .. 32 qd + 31 (qd = w & 3):
         // lane l < 16 the row of u_p, lane l + 16 the row of v_p, p = 16 qd + l
         // % 16.  Column block c (columns 32 c .. 32 c + 31: u_q, then v_q, q =
         // 16 c .. 16 c + 15) is needed for c <= qd (lower triangle); warp half
-        // hf = w >> 2 takes blocks hf and hf + 2, and hf = 1 also the y columns
-        // 128 (Re t) and 129 (Im t).
-        const int qd = warp & 3, hf = warp >> 2;
+        // hf = (w - NBUILD) >> 2 takes blocks hf and hf + 2, and hf = 1 also the
+        // y columns 128 (Re t) and 129 (Im t).
+        const int qd = warp & 3, hf = (warp - TcGram::NBUILD) >> 2;
         const bool is_u = lane < 16;
         const int p = 16 * qd + (lane & 15);
         const bool live = 16 * qd < D;   // some p of the quadrant is a feature
@@ -446,11 +448,14 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             const float other = __shfl_xor_sync(0xffffffffu, own_v, 16);
             return is_u ? own_u + other : other - own_u;
         };
-        auto kahan_block = [&](const float* v, uint64_t* s2, uint64_t* c2) {
+        // half hh of a column block: v[0..7] the u columns of q = 16 c + 8 hh
+        // .. + 7, v[8..15] their v columns
+        auto kahan_half = [&](const float* v, int hh, uint64_t* s2, uint64_t* c2) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float a = pair(v[2 * j], v[16 + 2 * j]);
-                const float b = pair(v[2 * j + 1], v[16 + 2 * j + 1]);
+            for (int jj = 0; jj < 4; ++jj) {
+                const int j = 4 * hh + jj;
+                const float a = pair(v[2 * jj], v[8 + 2 * jj]);
+                const float b = pair(v[2 * jj + 1], v[8 + 2 * jj + 1]);
                 const uint64_t y = f2sub(f2pack(a, b), c2[j]);
                 const uint64_t t = f2add(s2[j], y);
                 c2[j] = f2sub(f2sub(t, s2[j]), y);
@@ -458,14 +463,15 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             }
         };
         // record copy in shared memory: the u lanes write Re, the v lanes Im
-        auto put_block = [&](int c, const uint64_t* s2, const uint64_t* c2, const float* w) {
+        auto put_half = [&](int c, int hh, const uint64_t* s2, const uint64_t* c2, const float* w) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int jj = 0; jj < 4; ++jj) {
+                const int j = 4 * hh + jj;
                 float s0, s1, c0, c1;
                 f2unpack(s2[j], s0, s1);
                 f2unpack(c2[j], c0, c1);
-                const float v2[2] = {(s0 - c0) + pair(w[2 * j], w[16 + 2 * j]),
-                                     (s1 - c1) + pair(w[2 * j + 1], w[16 + 2 * j + 1])};
+                const float v2[2] = {(s0 - c0) + pair(w[2 * jj], w[8 + 2 * jj]),
+                                     (s1 - c1) + pair(w[2 * jj + 1], w[8 + 2 * jj + 1])};
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int q = 16 * c + 2 * j + h;
@@ -481,20 +487,23 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
             const uint32_t acc = lane_base + (uint32_t)(bs * TcGram::ACC_STRIDE);
-            // one column block at a time (registers)
-            float v[32];
-            auto ld_block = [&](uint32_t a) {
-                tc_ld16(a, v);
-                tc_ld16(a + 16, v + 16);
+            // half a column block at a time (registers)
+            float v[16];
+            auto ld_half = [&](uint32_t a, int hh) {
+                tc_ld8(a + 8 * hh, v);
+                tc_ld8(a + 16 + 8 * hh, v + 8);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             };
-            if (has0) {
-                ld_block(acc + 32 * hf);
-                kahan_block(v, sum2[0], comp2[0]);
-            }
-            if (has1) {
-                ld_block(acc + 32 * (hf + 2));
-                kahan_block(v, sum2[1], comp2[1]);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                if (has0) {
+                    ld_half(acc + 32 * hf, hh);
+                    kahan_half(v, hh, sum2[0], comp2[0]);
+                }
+                if (has1) {
+                    ld_half(acc + 32 * (hf + 2), hh);
+                    kahan_half(v, hh, sum2[1], comp2[1]);
+                }
             }
             if (need_y) {
                 tc_ld2(acc + 128, v);
@@ -511,21 +520,24 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             // end of the slice: add the cross terms (when the slice had more
             // than one chunk), write the record copy, release the accumulator
             const uint32_t sm = lane_base + (uint32_t)TcGram::SMALL_COL;
-            auto cross_block = [&](uint32_t a) {
+            auto cross_half = [&](uint32_t a, int hh) {
                 if (f.multi) {
-                    ld_block(a);
+                    ld_half(a, hh);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                    for (int j = 0; j < 16; ++j) v[j] = 0.f;
                 }
             };
-            if (has0) {
-                cross_block(sm + 32 * hf);
-                put_block(hf, sum2[0], comp2[0], v);
-            }
-            if (has1) {
-                cross_block(sm + 32 * (hf + 2));
-                put_block(hf + 2, sum2[1], comp2[1], v);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                if (has0) {
+                    cross_half(sm + 32 * hf, hh);
+                    put_half(hf, hh, sum2[0], comp2[0], v);
+                }
+                if (has1) {
+                    cross_half(sm + 32 * (hf + 2), hh);
+                    put_half(hf + 2, hh, sum2[1], comp2[1], v);
+                }
             }
             if (need_y) {
                 v[0] = 0.f;
@@ -546,15 +558,27 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
                 for (int j = 0; j < 8; ++j) { sum2[i][j] = 0ull; comp2[i][j] = 0ull; }
             sum_y = 0.f;
             comp_y = 0.f;
-            asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(NF) : "memory");
             // the record (NPK + D complex values, an even count for D = R^2,
             // so records start on 16-byte boundaries) in 16-byte pieces
             const float4* src = (const float4*)recs;
             float4* out = (float4*)(rec + (size_t)f.k * (NPK + D));
-            for (int x = tid; x < (NPK + D) / 2; x += NB) out[x] = src[x];
-            asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
+            for (int x = tid - 32 * TcGram::NBUILD; x < (NPK + D) / 2; x += NF) out[x] = src[x];
+            asm volatile("bar.sync 1, %0;" ::"n"(NF) : "memory");
         };
 
+        int g = 0;
+        for (TcChunk c = first_of(blockIdx.x, 0); c.valid; c = advance(c), ++g) {
+            TcFold f;
+            f.valid = true;
+            f.k = c.k;
+            f.gc = g;
+            f.last = c.last();
+            f.multi = c.idx > 0;
+            fold(f);
+        }
+    } else {
+        // ------------------------------------------------------- builder warps
         // operand rows of this thread: entries lane and 32 + lane (K blocks 0
         // and 1), features q = r8 + 8 j (j = 0..7) with r8 = w; the row of
         // u_q is 32 (q / 16) + q % 16 = 8 (4 (j / 2) + j % 2) + r8 and the row
@@ -621,8 +645,6 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
         };
 
         TcChunk cur = first_of(blockIdx.x, 0);
-        TcFold f1;   // chunk g-1, folded one chunk late
-        f1.valid = false;
         Vals vc;
         int g = 0;
         while (cur.valid) {
@@ -663,16 +685,9 @@ k_mid_gram_tc(const float2* __restrict__ H, const float2* __restrict__ Wm, const
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) tc_arrive(tc_smem_u32(&full[b]));
-            if (f1.valid) fold(f1);
-            f1.valid = true;
-            f1.k = cur.k;
-            f1.gc = g;
-            f1.last = cur.last();
-            f1.multi = cur.idx > 0;
             cur = nxt;
             ++g;
         }
-        if (f1.valid) fold(f1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

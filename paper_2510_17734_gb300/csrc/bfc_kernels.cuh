@@ -967,8 +967,7 @@ __device__ bool warp_chol(E* Lm, int D, S tol, int lane)
                     }
                 }
             }
-            continue;
-        }
+        } else {
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const int r = owned_row(s, lane);
@@ -1003,6 +1002,7 @@ __device__ bool warp_chol(E* Lm, int D, S tol, int lane)
                     rowp[q] = cur;
                 }
             }
+        }
         }
     }
     __syncwarp();
