@@ -57,8 +57,8 @@ WORKLOAD = ("n=65536 L=12 b=16 r=8, exp(i w rho)/rho line-to-line kernel, w=pi n
 TC_FLOPS_PER_ENTRY = 2 * 3 * 128 * 144   # flop, one contraction position x M 128 x N 144 x 3 products
 # DRAM counters of one k_mid_gram_tc launch (ncu, n = 32768, L = 11: 1,769,472
 # entries, 4096 slices), valid for the kernel source with this sha256 prefix
-TC_GRAM_TRAFFIC = {"source": "paper_2510_17734_gb300/csrc/bfc_gram_tc.cuh", "sha": "8cd2a90e9c15dfdc",
-                   "read_bytes": 240.755456e6, "write_bytes": 51.295744e6, "entries": 1769472, "slices": 4096}
+TC_GRAM_TRAFFIC = {"source": "paper_2510_17734_gb300/csrc/bfc_gram_tc.cuh", "sha": "90e721d0cb505251",
+                   "read_bytes": 241.090048e6, "write_bytes": 51.348736e6, "entries": 1769472, "slices": 4096}
 
 
 def kernel_source_sha(rel_path: str) -> str:
