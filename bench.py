@@ -57,7 +57,7 @@ WORKLOAD = ("n=65536 L=12 b=16 r=8, exp(i w rho)/rho line-to-line kernel, w=pi n
 TC_FLOPS_PER_ENTRY = 2 * 3 * 128 * 144   # flop, one contraction position x M 128 x N 144 x 3 products
 # DRAM counters of one k_mid_gram_tc launch (ncu, n = 32768, L = 11: 1,769,472
 # entries, 4096 slices), valid for the kernel source with this sha256 prefix
-TC_GRAM_TRAFFIC = {"source": "paper_2510_17734_gb300/csrc/bfc_gram_tc.cuh", "sha": "90e721d0cb505251",
+TC_GRAM_TRAFFIC = {"source": "paper_2510_17734_gb300/csrc/bfc_gram_tc.cuh", "sha": "8159f55fbacf40ac",
                    "read_bytes": 241.090048e6, "write_bytes": 51.348736e6, "entries": 1769472, "slices": 4096}
 
 

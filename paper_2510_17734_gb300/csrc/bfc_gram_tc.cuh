@@ -34,20 +34,21 @@
 // next slice starts.  A chunk issues only the k-steps (8 entries each) that
 // hold entries.
 //
-// Roles (one persistent CTA of 10 warps per SM; slices round-robin):
-//   warp 9       loader: bulk copies of every chunk's h rows, w rows and t
+// Roles (one persistent CTA of 18 warps per SM; slices round-robin):
+//   warp 17      loader: bulk copies of every chunk's h rows, w rows and t
 //                values into a 4-stage input ring
 //   warps 0..7   build the TF32 operand rows of chunk g from the ring in
-//                operand stage g&1, signal full[g&1]; then fold the hi*hi
-//                accumulator of chunk g-1 into the Kahan sums (tcgen05.ld,
-//                the column blocks of the lower triangle only), signal
-//                accempty, and at the end of a slice add its cross terms,
-//                signal sempty and write the record (through a shared-memory
-//                copy of the packed record, so the global stores are
-//                coalesced)
-//   warp 8       waits full[s] (and accempty / sempty when it reuses an
+//                operand stage g&1 and signal full[g&1]
+//   warp 16      waits full[s] (and accempty / sempty when it reuses an
 //                accumulator), issues the MMAs of the chunk, commits to
 //                empty[s] and accfull
+//   warps 8..15  (two per TMEM lane quadrant) fold the hi*hi accumulator of
+//                every chunk into the Kahan sums once its MMAs are complete
+//                (tcgen05.ld, the column blocks of the lower triangle only),
+//                signal accempty, and at the end of a slice add its cross
+//                terms, signal sempty and write the record (through a
+//                shared-memory copy of the packed record, so the global
+//                stores are coalesced)
 // Every mbarrier wait is bounded; on expiry the kernel raises *err, after
 // which all waits return at once (the work still runs to its end with the
 // same control flow in every warp, results undefined), then waits (bounded)
