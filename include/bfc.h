@@ -123,7 +123,7 @@ typedef struct {
     int32_t lr2bf_oversample; /* oversampling p of Alg. 2 for init_kind 2
                                (0 selects 5); r + p <= 32                   */
     double group_ratio;     /* gram_impl 0: groups-per-entry threshold of the
-                               grouped Gram.  0 selects the default (0.2
+                               grouped Gram.  0 selects the default (0.1
                                next to the tensor-core kernel, 0.9 next to
                                the CUDA-core one); < 0 never groups; > 0
                                is used as given                             */

@@ -408,10 +408,11 @@ static bfc_status create_impl(const bfc_params* params, const Inputs& in, bfc_ct
     c->gram_tc = c->fp32 && p.gram_impl != 1 && p.r <= 8;
     // grouped Gram (gram_impl 0) at the middle levels with few row / column
     // groups per entry: below this ratio against the tensor-core kernel (a
-    // group's compensated Kronecker update and its sums cost about what four
-    // to five entries cost there), below 0.9 against the per-entry CUDA-core
-    // kernel
-    c->grp_max_ratio = p.group_ratio > 0.0 ? p.group_ratio : (p.group_ratio < 0.0 ? 0.0 : 0.2);
+    // group's compensated Kronecker update and its sums cost about what seven
+    // entries cost there: at n = 65536 a level of 0.07 groups per entry is
+    // faster grouped, one of 0.14 on the tensor cores), below 0.9 against the
+    // per-entry CUDA-core kernel
+    c->grp_max_ratio = p.group_ratio > 0.0 ? p.group_ratio : (p.group_ratio < 0.0 ? 0.0 : 0.1);
     c->grp_cuda_ratio = p.group_ratio > 0.0 ? p.group_ratio : (p.group_ratio < 0.0 ? 0.0 : 0.9);
     bfc_status st = build(c, in);
     if (st != BFC_OK) {

@@ -57,7 +57,7 @@ def test_kernel_rooflines_arithmetic():
     p = synth.config(3)                     # n = 65536, L = 12, r = 8
     nnz, S = p.nnz, 1 << (p.L + 1)
     groups = bench.group_counts(p)
-    grouped = {m: g for m, g in groups.items() if g < 0.2 * nnz}
+    grouped = {m: g for m, g in groups.items() if g < 0.1 * nnz}
     nplain = p.L - len(grouped)
     prof = {"env_right": (24, 24 * 0.1), "mid_gram": (2 * nplain, 2 * nplain * 1.0),
             "mid_gram_grp": (4 * len(grouped), 2 * len(grouped) * 0.5), "mid_solve": (24, 24 * 0.5),

@@ -513,7 +513,7 @@ def test_full_size_orders_are_stable_sorts():
             np.testing.assert_array_equal(perm, np.lexsort((sub, key)))
             K = p.n if level in (0, p.L + 1) else 1 << (p.L + 1)
             np.testing.assert_array_equal(seg, np.searchsorted(np.sort(key), np.arange(K + 1)))
-        assert grouped == 6   # levels 1-3 and 10-12 have fewer than 0.2 groups per entry
+        assert grouped == 4   # levels 1, 2, 11 and 12 have fewer than 0.1 groups per entry
 
 
 def test_full_size_reported_errors_match_oracle(cfg3):
