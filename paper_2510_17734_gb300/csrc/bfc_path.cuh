@@ -190,7 +190,10 @@ template <typename T, int R> struct Path {
             }
             if (SC::MIXED) {
                 ProfScope ps(c, "mid_fallback", 2);
-                k_mid_fallback<T, R><<<gsolve, 32 * SC::WPB, SC::SMEM, c->stream>>>(
+                // a grid-stride loop over the listed slices (usually none): one
+                // wave of blocks at most
+                const unsigned gfb = std::min<unsigned>(gsolve, (unsigned)c->num_sms * SC::MINB);
+                k_mid_fallback<T, R><<<gfb, 32 * SC::WPB, SC::SMEM, c->stream>>>(
                     (const V*)c->rec, hin, c->seg[m], c->nxt[m], hout, c->Zd + (size_t)(m - 1) * S * R * R,
                     (V*)c->Zt + (size_t)(m - 1) * S * R * R, c->fb, c->P.lambda, c->ridge, c->d_count,
                     c->d_count + 3, c->fblist);
