@@ -61,6 +61,13 @@ TC_GRAM_TRAFFIC = {"source": "paper_2510_17734_gb300/csrc/bfc_gram_tc.cuh", "sha
                    "read_bytes": 241.090048e6, "write_bytes": 51.348736e6, "entries": 1769472, "slices": 4096}
 
 
+# DRAM counters of k_mid_solve at the n = 65536 workload itself (ncu, one-pass
+# metrics, mean of two launches of the first sweep: 3,774,874 entries, 8192
+# slices per level), valid for the kernel source with this sha256 prefix
+SOLVE_TRAFFIC = {"source": "paper_2510_17734_gb300/csrc/bfc_kernels.cuh", "sha": "ee9d36e694620396",
+                 "read_bytes": 427.399552e6, "write_bytes": 213.848576e6, "entries": 3774874, "slices": 8192}
+
+
 def kernel_source_sha(rel_path: str) -> str:
     import hashlib
     with open(os.path.join(ROOT, rel_path), "rb") as f:
@@ -195,8 +202,14 @@ def kernel_rooflines(prob, prof, stats, peaks, fp32_meas):
         fl = S * (4.0 / 3.0 * D ** 3 + 8.0 * D * D * (2 * (1 + steps_avg) + steps_avg)) + nnz * 8 * D
         a = by / (ms * 1e-3) / 1e9
         af = fl / (ms * 1e-3) / 1e12
+        cap = SOLVE_TRAFFIC
+        traffic = None
+        if nnz == cap["entries"] and S == cap["slices"] and kernel_source_sha(cap["source"]) == cap["sha"]:
+            traffic = cap["read_bytes"] + cap["write_bytes"]
         out.append({"kernel": "k_mid_solve", "bound": "hbm", "launch_ms": ms, "bytes": by,
-                    "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                    "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm, "traffic": traffic,
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at this "
+                                      f"workload (kernel source sha {cap['sha']})",
                     "flop": fl, "fp32_achieved_tflops": af, "fp32_peak": fp32_meas, "fp32_frac": af / fp32_meas,
                     "refine_steps_per_slice": steps_avg,
                     "per_unit": f"{(npk + D) * 8 + D * 24} B per slice (normal equations in, slice out) + "
