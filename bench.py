@@ -1009,7 +1009,7 @@ def run_bfc(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)   # about 1 s timed: several clock samples at 200 ms
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="bfc", choices=["bfc", "reference"])
     ap.add_argument("--prec", default="c64", choices=["c64", "fp64"])
