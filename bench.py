@@ -789,20 +789,22 @@ def run_reference(args, rank, world):
     prob = synth.config(3)
     X0 = synth.random_factors(prob.n, prob.L, prob.r, prob.seed + synth.SEED_PLANT, sigma=0.3)
     cores = host_cores()
-    # each step: the oracle (OpenMP variant, all host cores) sweeps a quarter
-    # of the training entries (every 4th) at the full shape, all slices and
-    # fibers solved; warm-up steps sweep 1 %
+    # each step: the oracle (OpenMP variant, all host cores) sweeps every
+    # stride-th training entry at the full shape, all slices and fibers
+    # solved; the stride (4 up to 15 steps, larger beyond) keeps the whole run
+    # to a few minutes; warm-up steps sweep 1 %
+    stride = 4 * max(1, -(-args.steps // 15))
     for _ in range(args.warmup):
         time_oracle_sweep(prob, X0, 100, threads=cores)
     times = []
     m = 0
     for _ in range(args.steps):
-        m, dt = time_oracle_sweep(prob, X0, 4, threads=cores)
+        m, dt = time_oracle_sweep(prob, X0, stride, threads=cores)
         times.append(dt)
     t_step = statistics.mean(times)
     value = m / t_step
     sample = (f"each step: one oracle ALS sweep (complex128, OpenMP variant on {cores} host threads, "
-              f"bit-identical to the serial oracle) over every 4th training entry ({m} entries) at the full "
+              f"bit-identical to the serial oracle) over every {stride}th training entry ({m} entries) at the full "
               f"n=65536 L=12 r=8 shape, all 98304 slice and 131072 fiber systems solved; {t_step:.2f} s per "
               "step; warm-up steps sweep 1 %")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
