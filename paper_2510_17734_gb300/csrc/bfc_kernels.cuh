@@ -1480,7 +1480,7 @@ k_mid_fallback(const typename cvec<T>::type* __restrict__ rec, const typename cv
                typename cvec<T>::type* __restrict__ Hn, double2* __restrict__ Zd,
                typename cvec<T>::type* __restrict__ Zt, double2* __restrict__ fb, double lambda_in, double ridge,
                unsigned long long* __restrict__ nsing, const unsigned long long* __restrict__ nfb,
-               const int32_t* __restrict__ fblist)
+               const int32_t* __restrict__ fblist, unsigned long long* __restrict__ nfb_sweep)
 {
     typedef typename cvec<T>::type V;
     typedef SolveCfg<T, R> C;
@@ -1489,6 +1489,9 @@ k_mid_fallback(const typename cvec<T>::type* __restrict__ rec, const typename cv
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     V* zt_s = (V*)(smem + (size_t)wib * C::WBYTES);
     const long long count = (long long)*nfb;
+    // the level's fallbacks join the sweep's count (one thread; nothing else
+    // writes it while this kernel runs)
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nfb_sweep += (unsigned long long)count;
     for (long long idx = (long long)blockIdx.x * C::WPB + wib; idx < count; idx += (long long)gridDim.x * C::WPB) {
         const int k = fblist[idx];
         const V* K = rec + (size_t)k * (NPK + D);

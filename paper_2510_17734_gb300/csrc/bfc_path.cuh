@@ -189,15 +189,14 @@ template <typename T, int R> struct Path {
                     c->d_count + 3, c->d_count + 2, c->fblist, (int)S, c->d_count + 5, c->inject == 1 ? 1 : 0);
             }
             if (SC::MIXED) {
-                ProfScope ps(c, "mid_fallback", 2);
+                ProfScope ps(c, "mid_fallback");
                 // a grid-stride loop over the listed slices (usually none): one
                 // wave of blocks at most
                 const unsigned gfb = std::min<unsigned>(gsolve, (unsigned)c->num_sms * SC::MINB);
                 k_mid_fallback<T, R><<<gfb, 32 * SC::WPB, SC::SMEM, c->stream>>>(
                     (const V*)c->rec, hin, c->seg[m], c->nxt[m], hout, c->Zd + (size_t)(m - 1) * S * R * R,
                     (V*)c->Zt + (size_t)(m - 1) * S * R * R, c->fb, c->P.lambda, c->ridge, c->d_count,
-                    c->d_count + 3, c->fblist);
-                launch_add_u64(c->d_count + 1, c->d_count + 3, c->stream);  // fallbacks of the sweep
+                    c->d_count + 3, c->fblist, c->d_count + 1);   // + the fallbacks of the sweep
             }
         }
         BFC_LAUNCH_CHECK(c, "middle levels");

@@ -322,12 +322,6 @@ __global__ void k_axpby(double* __restrict__ y, double a, const double* __restri
     if (q < n) y[q] = a * x[q] + b * z[q];
 }
 
-// *dst += *src for device counters
-__global__ void k_add_u64(unsigned long long* __restrict__ dst, const unsigned long long* __restrict__ src)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) *dst += *src;
-}
-
 // ------------------------------------------------------------ launchers
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -372,10 +366,6 @@ void launch_dot(const double* a, const double* b, int64_t n, double* part, int n
 void launch_axpby(double* y, double a, const double* x, double b, const double* z, int64_t n, cudaStream_t st)
 {
     if (n > 0) k_axpby<<<nblk(n, 256), 256, 0, st>>>(y, a, x, b, z, n);
-}
-void launch_add_u64(unsigned long long* dst, const unsigned long long* src, cudaStream_t st)
-{
-    k_add_u64<<<1, 32, 0, st>>>(dst, src);
 }
 void launch_invert(const int32_t* perm, int64_t N, int32_t* pos, cudaStream_t st)
 {

@@ -30,7 +30,6 @@ void launch_all_keys(const int32_t* ii, const int32_t* jj, int64_t M, int L, int
 void launch_dot(const double* a, const double* b, int64_t n, double* part, int nblocks, double* out,
                 cudaStream_t st);
 void launch_axpby(double* y, double a, const double* x, double b, const double* z, int64_t n, cudaStream_t st);
-void launch_add_u64(unsigned long long* dst, const unsigned long long* src, cudaStream_t st);
 void launch_invert(const int32_t* perm, int64_t N, int32_t* pos, cudaStream_t st);
 void launch_compose(const int32_t* perm, const int32_t* pos_other, int64_t N, int32_t* out, cudaStream_t st);
 void launch_gather_i32(const int32_t* src, const int32_t* perm, int64_t N, int32_t* out, cudaStream_t st);

@@ -168,10 +168,11 @@ def test_one_sweep_parity(request, which, prec):
         xo = oracle.eval_entries(p.n, p.L, p.b, p.r, Xo, p.it, p.jt)
         assert rel_dev(xg, xp) <= rel_dev(xo, xp) + tol
     # kernels per sweep: 1 + L right environments, 3 + 3 outer fiber kernels,
-    # per middle level Gram + solve (+ FP64 fallback + counter in the
-    # precision form), residual reduction, 2 for ||S||^2, 2 for the test error;
+    # per middle level Gram + solve (+ the FP64 fallback, which also counts
+    # the level's fallbacks, in the precision form), residual reduction, 2 for
+    # ||S||^2, 2 for the test error;
     # a middle level on the grouped Gram runs two kernels for its Gram
-    per_level = 4 if prec == bfc.PREC_C64 else 2
+    per_level = 3 if prec == bfc.PREC_C64 else 2
     n_grouped = prof.get("mid_gram_grp", (0, 0.0))[0] // 2
     assert st["launches"] == 12 + (1 + per_level) * p.L + n_grouped
 
