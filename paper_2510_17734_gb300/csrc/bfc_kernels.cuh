@@ -1599,17 +1599,29 @@ k_eval(const int32_t* __restrict__ ii, const int32_t* __restrict__ jj, int64_t M
         const int i = valid ? ii[e] : 0, j = valid ? jj[e] : 0;   // entry 0's indices stand in for the tail
         V h = col ? z1[(size_t)i * R + c] : czero<V>();
         const int pi = i / b, pj = j / b;
-        for (int m = 1; m <= L; ++m) {
+        // the slice of every level depends only on (i, j): level m + 1's
+        // column is fetched while level m is formed, so the L2 latency of the
+        // gathers leaves the chain of dependent levels
+        auto fetch = [&](int m, V* zc) {
             const V* Zk = Z + ((size_t)(m - 1) * S + slice_of(pi, pj, m, L)) * R * R;
+#pragma unroll
+            for (int a = 0; a < R; ++a) zc[a] = col ? Zk[a * R + c] : czero<V>();
+        };
+        V zcur[R], znext[R];
+        if (L >= 1) fetch(1, zcur);
+        for (int m = 1; m <= L; ++m) {
+            if (m < L) fetch(m + 1, znext);
             V acc = czero<V>();
 #pragma unroll
             for (int a = 0; a < R; ++a) {
                 V ha;
                 ha.x = __shfl_sync(0xffffffffu, h.x, a, GS);
                 ha.y = __shfl_sync(0xffffffffu, h.y, a, GS);
-                if (col) cmac(acc, ha, Zk[a * R + c]);
+                if (col) cmac(acc, ha, zcur[a]);
             }
             h = acc;
+#pragma unroll
+            for (int a = 0; a < R; ++a) zcur[a] = znext[a];
         }
         V x = czero<V>();
 #pragma unroll

@@ -115,7 +115,7 @@ template <typename T, int R> struct Path {
                                                                        c->jL, N);
         }
         BFC_LAUNCH_CHECK(c, "env_init");
-        const unsigned g = (unsigned)(S < 152 * 16 ? S : 152 * 16);
+        const unsigned g = (unsigned)(S < (int64_t)c->num_sms * 16 ? S : (int64_t)c->num_sms * 16);
         for (int m = c->L; m >= 1; --m) {
             ProfScope ps(c, "env_right");
             k_env_right<T, R><<<g, 128, 0, c->stream>>>(W + (size_t)m * NR, W + (size_t)(m - 1) * NR,
@@ -229,7 +229,7 @@ template <typename T, int R> struct Path {
                                                                      G1, part);
         }
         BFC_LAUNCH_CHECK(c, "grad_rows");
-        const unsigned g = (unsigned)(S < 152 * 16 ? S : 152 * 16);
+        const unsigned g = (unsigned)(S < (int64_t)c->num_sms * 16 ? S : (int64_t)c->num_sms * 16);
         for (int m = 1; m <= L; ++m) {
             const int in = (m - 1) & 1, out = m & 1;
             ProfScope ps(c, "grad_mid");
