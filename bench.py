@@ -64,14 +64,23 @@ TC_GRAM_TRAFFIC = {"source": "paper_2510_17734_gb300/csrc/bfc_gram_tc.cuh", "sha
 # DRAM counters of k_mid_solve at the n = 65536 workload itself (ncu, one-pass
 # metrics, mean of two launches of the first sweep: 3,774,874 entries, 8192
 # slices per level), valid for the kernel source with this sha256 prefix
-SOLVE_TRAFFIC = {"source": "paper_2510_17734_gb300/csrc/bfc_kernels.cuh", "sha": "ee9d36e694620396",
+SOLVE_TRAFFIC = {"source": "paper_2510_17734_gb300/csrc/bfc_kernels.cuh", "sha": "fca9bdd68955b392",
+                 # the kernel and the device functions it calls (warp_chol ... k_mid_solve)
+                 "span": ("// Row of slot s owned by a lane in the warp-level factorization",
+                          "// FP64 fallback of the precision form"),
                  "read_bytes": 427.399552e6, "write_bytes": 213.848576e6, "entries": 3774874, "slices": 8192}
 
 
-def kernel_source_sha(rel_path: str) -> str:
+def kernel_source_sha(rel_path: str, span=None) -> str:
+    """sha256 prefix of a source file, or of the text between two markers."""
     import hashlib
     with open(os.path.join(ROOT, rel_path), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+        data = f.read()
+    if span:
+        txt = data.decode()
+        a, b = txt.index(span[0]), txt.index(span[1])
+        data = txt[a:b].encode()
+    return hashlib.sha256(data).hexdigest()[:16]
 
 
 def load_peaks():
@@ -204,12 +213,13 @@ def kernel_rooflines(prob, prof, stats, peaks, fp32_meas):
         af = fl / (ms * 1e-3) / 1e12
         cap = SOLVE_TRAFFIC
         traffic = None
-        if nnz == cap["entries"] and S == cap["slices"] and kernel_source_sha(cap["source"]) == cap["sha"]:
+        if nnz == cap["entries"] and S == cap["slices"] and \
+                kernel_source_sha(cap["source"], cap["span"]) == cap["sha"]:
             traffic = cap["read_bytes"] + cap["write_bytes"]
         out.append({"kernel": "k_mid_solve", "bound": "hbm", "launch_ms": ms, "bytes": by,
                     "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm, "traffic": traffic,
                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at this "
-                                      f"workload (kernel source sha {cap['sha']})",
+                                      f"workload (kernel source sha {cap['sha']}: warp_chol through k_mid_solve)",
                     "flop": fl, "fp32_achieved_tflops": af, "fp32_peak": fp32_meas, "fp32_frac": af / fp32_meas,
                     "refine_steps_per_slice": steps_avg,
                     "per_unit": f"{(npk + D) * 8 + D * 24} B per slice (normal equations in, slice out) + "
