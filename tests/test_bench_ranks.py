@@ -107,3 +107,24 @@ def test_reference_arm_json_line():
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_constants_are_keyed_to_their_kernel_sources():
+    """The measured DRAM traffic the bench reports belongs to a kernel's source
+    as it was captured: the tensor-core Gram by its whole file, the solve by
+    the span from warp_chol through k_mid_solve.  A change inside the span
+    (simulated on a copy) changes the key, one outside it does not."""
+    import hashlib
+    for cap in (bench.TC_GRAM_TRAFFIC, bench.SOLVE_TRAFFIC):
+        assert bench.kernel_source_sha(cap["source"], cap.get("span")) == cap["sha"]
+    cap = bench.SOLVE_TRAFFIC
+    with open(os.path.join(bench.ROOT, cap["source"])) as f:
+        txt = f.read()
+    a = txt.index(cap["span"][0])
+
+    def key(t):
+        return hashlib.sha256(t[t.index(cap["span"][0]):t.index(cap["span"][1])].encode()).hexdigest()[:16]
+
+    assert key(txt) == cap["sha"]
+    assert key(txt + "// outside\n") == cap["sha"]
+    assert key(txt[:a + 10] + "x" + txt[a + 10:]) != cap["sha"]
