@@ -70,7 +70,10 @@ template <typename V, int R> struct GrpRec {
 };
 
 // Shared-memory budget of k_group_sums: a block's entries (rows of the
-// summed side and values) are staged when they fit.
+// summed side and values) are staged when they fit.  CAP is the most a block
+// stages (SMEM bytes); a launch sizes its dynamic shared memory for the
+// level's largest block, at most CAP entries, so levels with small groups
+// keep more blocks resident.
 template <typename T, int R> struct GsumCfg {
     static constexpr int NTH = 128;
     static constexpr int GB = NTH / R;                    // groups per block
